@@ -1,0 +1,330 @@
+"""Throughput benchmark of the hole-transport step (Eq. 6 pair sum + Fig. 2 step).
+
+Default workload: one event of 1,048,576 holes -- 16 parallel straight
+muon-like tracks of 65,536 holes, 30 um apart, crossing the 675 um CCD -- with
+the FP32 + Kahan pair sum and FP64 positions.  A "step" is one time step of
+the whole path: Eq. 6 pair sum, integrate (Eqs. 1-4, Philox diffusion,
+update, collection, binning), compaction and bookkeeping.
+
+Prints ONE JSON line: pair-interactions/s (value) and carrier-steps/s, the
+pair kernel's live roofline fraction, the oracle CPU baseline, an end-to-end
+figure through the C ABI with host buffers, clocks sampled during the timed
+region, and the FP64 form timed on a sub-sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_11043_gb300 import inputs  # noqa: E402
+
+FP32_OPS_PER_PAIR = 11  # 3 sub + 3 fma (r^2) + 2 mul (r^-3) + 3 fma (accumulate); rsqrt on MUFU
+FP32_LANES_PER_SM = 128
+METRIC = "pair-interactions/s"
+WORKLOAD = ("track-bundle-1M: one event of 1,048,576 holes in 16 straight muon-like tracks "
+            "(65,536 holes each, 2.5 mm long, 0.5 um jitter, 30 um apart) across a 675 um CCD; "
+            "E = 2 z - 1500 V/cm, T = 140 K, dt = 10 ps, eps = 0.01 um, 512 x 512 pixels of 15 um")
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+def cpu_baseline(wl, seconds: float = 12.0):
+    """The FP64 oracle as it stands, on this host's cores: the Eq. 6 sum plus
+    the rest of the step for a bounded sample of carriers of the same event."""
+    import oracle as O
+    p = O.make_params(img_w=wl.img_w, img_h=wl.img_h)
+    src = np.arange(wl.n, dtype=np.int64)
+    rng = np.random.default_rng(0)
+    m = 8
+    while True:
+        tg = np.sort(rng.choice(wl.n, size=m, replace=False))
+        t0 = time.perf_counter()
+        O.step_targets(p, wl.xyz, src, tg, int(wl.seeds[0]), 1)
+        dt = time.perf_counter() - t0
+        if dt > 0.5 or m >= wl.n:
+            break
+        m = min(wl.n, m * 4)
+    m = int(min(wl.n, max(m, m * seconds / max(dt, 1e-3))))
+    tg = np.sort(rng.choice(wl.n, size=m, replace=False))
+    t0 = time.perf_counter()
+    O.step_targets(p, wl.xyz, src, tg, int(wl.seeds[0]), 1)
+    dt = time.perf_counter() - t0
+    return {"value": m * wl.n / dt, "unit": "pairs/s", "cores": O.num_threads(), "kind": "oracle",
+            "carrier_steps_per_s": m / dt,
+            "sample": f"one step (Eq. 6 field from all {wl.n} holes + drift/diffusion/update) for {m} "
+                      f"randomly chosen holes of the same event: {m * wl.n:.3e} pair terms in {dt:.1f} s"}
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 CPU oracle on the same workload, bounded steps."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    wl = inputs.track_bundle()
+    per_step = max(2.0, min(4.0, 150.0 / max(1, args.steps + args.warmup)))
+    import oracle as O
+    p = O.make_params(img_w=wl.img_w, img_h=wl.img_h)
+    src = np.arange(wl.n, dtype=np.int64)
+    rng = np.random.default_rng(0)
+    # size the per-step sample to ~per_step seconds
+    m = 16
+    t0 = time.perf_counter()
+    O.step_targets(p, wl.xyz, src, np.arange(m), int(wl.seeds[0]), 1)
+    dt = time.perf_counter() - t0
+    m = int(min(wl.n, max(16, m * per_step / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        O.step_targets(p, wl.xyz, src, np.sort(rng.choice(wl.n, m, replace=False)), int(wl.seeds[0]), 1)
+    total = 0.0
+    for s in range(args.steps):
+        tg = np.sort(rng.choice(wl.n, m, replace=False))
+        t0 = time.perf_counter()
+        O.step_targets(p, wl.xyz, src, tg, int(wl.seeds[0]), s + 1)
+        total += time.perf_counter() - t0
+    pairs = args.steps * m * wl.n
+    value = pairs / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_carriers": wl.n},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{m} randomly chosen holes per step, field from all {wl.n}"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import paper_2203_11043_gb300 as gc
+    from paper_2203_11043_gb300 import build
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    gc.load()
+    stream = torch.cuda.current_stream()
+    sms, ccmaj, ccmin = gc.gc_device_info()
+
+    wl = inputs.track_bundle()
+    # every rank runs an independent replica of the event (replicas only: the
+    # single event is not sharded); seeds differ per rank
+    seeds = wl.seeds + np.uint64(rank)
+    params = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
+                                  graph_steps=1, timing=1)
+    sim = gc.Simulation(params, wl.xyz, wl.ev_off, seeds, wl.img_origin, stream=stream.cuda_stream)
+    st0 = sim.stats()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        sim.run(1)
+    torch.cuda.synchronize()
+    base = sim.stats()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (256 MB > 129 MB L2)
+            starts[k].record(stream)
+            sim.run(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    after = sim.stats()
+    pairs = after["pair_interactions"] - base["pair_interactions"]
+    csteps = after["carrier_steps"] - base["carrier_steps"]
+    pair_ms = after["pair_kernel_ms"] - base["pair_kernel_ms"]
+    pair_launches = after["pair_kernel_launches"] - base["pair_kernel_launches"]
+    steps_done = after["steps"] - base["steps"]
+    if world > 1:
+        t = torch.tensor([total_ms, pairs, csteps], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        total_ms, pairs, csteps = float(mx[0]), float(t[1]), float(t[2])
+    value = pairs / (total_ms / 1e3)
+    clocks = clk.summary()
+
+    peaks = measured_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * FP32_LANES_PER_SM * max_mhz * 1e6 / FP32_OPS_PER_PAIR
+    pairs_per_launch = pairs / max(1, pair_launches) / max(1, world)
+    achieved = pairs_per_launch / (pair_ms / max(1, pair_launches) / 1e3) if pair_launches else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "pair_fp32_kernel<R,Kahan>",
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz "
+                              f"(sm_max_mhz of MEASURED_PEAKS.json) / {FP32_OPS_PER_PAIR} FP32 ops per pair",
+                "frac_at_sampled_clock": ((achieved / (peak * clocks["sm_mhz"] / max_mhz))
+                                          if achieved and clocks.get("sm_mhz") else None),
+                "pair_kernel_share_of_step": pair_ms / max(total_ms, 1e-9)}
+
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_carriers": wl.n, "events": 1,
+                       "precision": "FP32 pair sum with Kahan across j-tiles; FP64 positions",
+                       "pair_R": after["pair_variant"], "pair_blocks": after["pair_blocks"],
+                       "jchunk": after["jchunk"], "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}", "device": f"sm_{ccmaj}{ccmin}, {sms} SMs"},
+            "carrier_steps_per_s": csteps / (total_ms / 1e3), "steps_done": steps_done,
+            "roofline": roofline, "gpu_launches": int(steps_done * after["launches_per_step"]),
+            "clocks": clocks}
+
+    # FP64 form vs FP32 form on one track of the same workload (like for like)
+    if not args.no_fp64 and rank == 0:
+        sub = inputs.subsample(wl, 65536, seed=3)
+        forms = {}
+        for name, prec in (("fp64", gc.GC_FP64), ("fp32_kahan", gc.GC_FP32_KAHAN)):
+            p = gc.gc_default_params(precision=prec, img_w=wl.img_w, img_h=wl.img_h, graph_steps=1,
+                                     timing=1)
+            with gc.Simulation(p, sub.xyz, sub.ev_off, sub.seeds, sub.img_origin,
+                               stream=stream.cuda_stream) as s2:
+                s2.run(2)
+                b = s2.stats()
+                s2.run(3)
+                a = s2.stats()
+                forms[name] = (a["pair_interactions"] - b["pair_interactions"]) / (
+                    (a["pair_kernel_ms"] - b["pair_kernel_ms"]) / 1e3)
+        line["fp64_form"] = {"pair_kernel_pairs_per_s": forms["fp64"],
+                             "fp32_kahan_pair_kernel_pairs_per_s": forms["fp32_kahan"],
+                             "fp32_over_fp64": forms["fp32_kahan"] / forms["fp64"],
+                             "workload": "65,536 holes drawn from the same bundle, 3 steps"}
+
+    # end to end through the C ABI with host buffers (H2D load, steps, D2H results)
+    if not args.no_e2e:
+        e2e_steps = min(args.steps, 20)
+        p = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
+                                 graph_steps=min(32, e2e_steps), autotune=0,
+                                 pair_R=after["pair_variant"], jchunk=after["jchunk"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with gc.Simulation(p, wl.xyz, wl.ev_off, seeds, wl.img_origin, stream=stream.cuda_stream) as s3:
+            s3.run(e2e_steps)
+            res = s3.collect()
+            img = s3.image()
+            st3 = s3.stats()
+        t1 = time.perf_counter()
+        h2d = wl.xyz.nbytes + 8 * wl.n  # FP64 positions, active-id list and event map
+        d2h = res["final_xy"].nbytes + res["collect_step"].nbytes + img.nbytes
+        e2e_val = st3["pair_interactions"] / (t1 - t0)
+        if world > 1:
+            t = torch.tensor([t1 - t0, st3["pair_interactions"]], dtype=torch.float64, device="cuda")
+            mx = t.clone()
+            torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+            e2e_val = float(t[1]) / float(mx[0])
+        line["e2e"] = {"value": e2e_val, "unit": "pairs/s",
+                       "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+                       "steps": e2e_steps,
+                       "includes": "gc_create + gc_load_carriers (host positions) + gc_run + gc_collect + "
+                                   "gc_image (host outputs), host wall clock"}
+
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

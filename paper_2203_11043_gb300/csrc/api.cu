@@ -1,0 +1,814 @@
+// api.cu -- the C ABI of libgcoreccd (declared in include/gcoreccd.h).
+//
+// Host orchestration only: parameter validation, the load-time layout
+// (events ordered largest first so that pair work items come out in
+// longest-processing-time order), the step-0 pass, the pair-kernel
+// autotuner, CUDA-graph capture of the step loop, and copies in and out.
+// Every step of the transport itself runs in the kernels of pair.cu and
+// step.cu.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gcoreccd.h"
+#include "gc_internal.cuh"
+#include "gc_launch.h"
+
+using namespace gc;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+gc_status cuda_fail(cudaError_t e) {
+    std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return GC_ERR_NO_DEVICE;
+    if (e == cudaErrorMemoryAllocation) return GC_ERR_ALLOC;
+    return GC_ERR_CUDA;
+}
+
+#define GC_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_);   \
+    } while (0)
+
+// CODATA 2018 exact SI values and eps0.
+constexpr double kQ = 1.602176634e-19;
+constexpr double kKB = 1.380649e-23;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+gc_status validate(const gc_params *p) {
+    if (!p || p->abi_version != GC_ABI_VERSION) return GC_ERR_PARAM;
+    if (p->precision < GC_FP64 || p->precision > GC_FP32_KAHAN) return GC_ERR_PARAM;
+    const double v[] = {p->thickness_um, p->z_well_um, p->a1_V_cm_um, p->a2_V_cm, p->T_K,
+                        p->eps_si_rel, p->softening_um, p->dt_s, p->pixel_um};
+    for (double x : v)
+        if (!is_finite(x)) return GC_ERR_PARAM;
+    if (!(p->thickness_um > 0) || !(p->T_K > 0) || !(p->dt_s > 0) || !(p->pixel_um > 0))
+        return GC_ERR_PARAM;
+    if (p->z_well_um >= p->thickness_um) return GC_ERR_PARAM;
+    if (p->max_steps < 0 || p->max_steps > INT_MAX) return GC_ERR_PARAM;
+    if (p->img_w <= 0 || p->img_h <= 0 || (int64_t)p->img_w * p->img_h > (1 << 26))
+        return GC_ERR_PARAM;
+    if (p->coulomb && (!(p->softening_um > 0) || !(p->eps_si_rel > 0))) return GC_ERR_PARAM;
+    if (p->graph_steps < 0 || p->graph_steps > 4096) return GC_ERR_PARAM;
+    if (p->jchunk < 0) return GC_ERR_PARAM;
+    if ((p->coulomb | p->diffusion | p->reflect_back | p->autotune | p->newton | p->timing) & ~1)
+        return GC_ERR_PARAM;
+    if (p->pair_R != 0 && p->pair_R != 2 && p->pair_R != 4 && p->pair_R != 8) return GC_ERR_PARAM;
+    return GC_OK;
+}
+
+Phys make_phys(const gc_params &p) {
+    Phys ph{};
+    ph.a1 = p.a1_V_cm_um;
+    ph.a2 = p.a2_V_cm;
+    ph.thickness = p.thickness_um;
+    ph.z_well = p.z_well_um;
+    ph.dt = p.dt_s;
+    // Eq. 6: K = q / (4 pi eps0 eps_r) [V m]; 1/um^2 = 1e12/m^2 and 1 V/m = 1e-2 V/cm.
+    ph.K = kQ / (4.0 * kPi * kEps0 * p.eps_si_rel) * 1e10;
+    ph.eps2 = p.softening_um * p.softening_um;
+    // Eq. 2 constants.
+    ph.mu0 = 1.31e8 * std::pow(p.T_K, -2.2);
+    ph.inv_Ec = 1.0 / (1.24 * std::pow(p.T_K, 1.68));
+    ph.beta = 0.46 * std::pow(p.T_K, 0.17);
+    ph.inv_beta = 1.0 / ph.beta;
+    ph.Vth = kKB * p.T_K / kQ;  // Eq. 4
+    ph.pixel = p.pixel_um;
+    ph.img_w = p.img_w;
+    ph.img_h = p.img_h;
+    ph.coulomb = p.coulomb;
+    ph.diffusion = p.diffusion;
+    ph.reflect = p.reflect_back;
+    return ph;
+}
+
+struct DevAllocs {
+    std::vector<void *> ptrs;
+    cudaError_t alloc(void **p, size_t bytes) {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 16);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    void release() {
+        for (void *p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+int round_up(long long v, int m) { return (int)((v + m - 1) / m * m); }
+
+// j-chunk length: one chunk per event when the i-tiles alone give every
+// resident block >= 32 items; otherwise split j so that they do (at most 32
+// chunks), keeping dynamic-scheduling tail loss near 1/64 of a step.
+int choose_jchunk(const std::vector<long long> &sizes, int R, int small_n, int slots, int user) {
+    long long n_max = 1;
+    for (long long n : sizes) n_max = std::max(n_max, n);
+    if (user > 0) return round_up(user, kTileJ);
+    long long tiles = 0;
+    for (long long n : sizes)
+        if (n > 0) tiles += (n + itile_for(R, lanes_for((int)n, small_n)) - 1) /
+                            itile_for(R, lanes_for((int)n, small_n));
+    const long long want = 32LL * std::max(slots, 1);
+    long long js = tiles >= want ? 1 : std::min<long long>(32, (want + tiles - 1) / std::max(tiles, 1LL));
+    return round_up((n_max + js - 1) / js, kTileJ);
+}
+
+}  // namespace
+
+struct gc_sim {
+    gc_params p;
+    Phys phys;
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool loaded = false;
+    int64_t n = 0, E = 0;
+    std::vector<int64_t> user_off;   // caller's event offsets
+    DevAllocs mem;
+    Dev dev{};
+    Ctrl *h_ctrl = nullptr;          // pinned mirror of the device control block
+    long long *h_limit = nullptr;    // pinned staging for step_limit
+    cudaGraphExec_t graph = nullptr;
+    int integ_grid = 1;
+    int launches_per_step = 0;
+    long long part_cap_chunks = 1;   // j-chunks the partial buffer can hold
+    std::vector<cudaEvent_t> ev_a, ev_b;  // timing: around each pair launch of a graph
+    double pair_ms = 0.0;
+    long long pair_launches = 0;
+};
+
+namespace {
+
+bool fp64_mode(const gc_sim *s) { return s->p.precision == GC_FP64; }
+
+void free_state(gc_sim *s) {
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    for (cudaEvent_t e : s->ev_a) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->ev_b) cudaEventDestroy(e);
+    s->ev_a.clear();
+    s->ev_b.clear();
+    s->pair_ms = 0.0;
+    s->pair_launches = 0;
+    s->mem.release();
+    s->loaded = false;
+    s->dev = Dev{};
+}
+
+// One time step; k indexes the step inside a captured graph (timing events).
+gc_status enqueue_step(gc_sim *s, int k) {
+    const bool f64 = fp64_mode(s);
+    const bool timed = s->p.timing && s->phys.coulomb && k < (int)s->ev_a.size();
+    if (timed) GC_CUDA(cudaEventRecord(s->ev_a[k], s->stream));
+    if (s->phys.coulomb) GC_CUDA(launch_pair(s->dev, s->p.precision, s->p.newton, s->stream));
+    if (timed) GC_CUDA(cudaEventRecord(s->ev_b[k], s->stream));
+    GC_CUDA(launch_integrate(s->dev, f64, false, s->integ_grid, s->stream));
+    GC_CUDA(launch_compact(s->dev, f64, s->integ_grid, s->stream));
+    GC_CUDA(launch_finalize(s->dev, false, s->stream));
+    return GC_OK;
+}
+
+gc_status read_ctrl(gc_sim *s) {
+    GC_CUDA(cudaMemcpyAsync(s->h_ctrl, s->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
+    GC_CUDA(cudaStreamSynchronize(s->stream));
+    return GC_OK;
+}
+
+gc_status set_limit(gc_sim *s, long long limit) {
+    *s->h_limit = limit;
+    GC_CUDA(cudaMemcpyAsync(&s->dev.ctrl->step_limit, s->h_limit, sizeof(long long),
+                            cudaMemcpyHostToDevice, s->stream));
+    GC_CUDA(cudaStreamSynchronize(s->stream));
+    return GC_OK;
+}
+
+gc_status capture_graph(gc_sim *s) {
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    if (s->p.graph_steps <= 0) return GC_OK;
+    cudaGraph_t g = nullptr;
+    GC_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    gc_status st = GC_OK;
+    for (int k = 0; k < s->p.graph_steps && st == GC_OK; ++k) st = enqueue_step(s, k);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (st != GC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return GC_OK;
+}
+
+// Pick R (and the grid and j-chunk that follow from it) for the FP32 pair
+// kernel.  With autotune on, each candidate is timed on the loaded carriers.
+gc_status choose_shape(gc_sim *s, const std::vector<long long> &sizes) {
+    PairShape best = s->dev.shape;
+    if (fp64_mode(s)) {
+        const int occ = std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0));
+        best.R = 1;
+        best.small_n = 0;
+        best.n_blocks = s->sm_count * occ;
+        long long n_max = 1;
+        for (long long n : sizes) n_max = std::max(n_max, n);
+        best.jchunk = round_up(n_max, kTileJ);  // one chunk: j summed in ascending order
+        s->dev.shape = best;
+        return GC_OK;
+    }
+    int cands[3] = {2, 4, 8};
+    float best_ms = 1e30f;
+    bool tune = s->p.autotune && s->phys.coulomb && s->n > 0 && s->p.pair_R == 0;
+    int first = tune ? 0 : 1, last = tune ? 2 : 1;
+    if (s->p.pair_R != 0) cands[1] = s->p.pair_R;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (tune) {
+        GC_CUDA(cudaEventCreate(&a));
+        GC_CUDA(cudaEventCreate(&b));
+    }
+    for (int ci = first; ci <= last; ++ci) {
+        PairShape sh;
+        sh.R = cands[ci];
+        sh.small_n = 8192;
+        const int occ = std::max(1, pair_kernel_occupancy(s->p.precision, sh.R, s->p.newton));
+        sh.n_blocks = s->sm_count * occ;
+        sh.jchunk = choose_jchunk(sizes, sh.R, sh.small_n, sh.n_blocks, s->p.jchunk);
+        long long n_max = 1;
+        for (long long n : sizes) n_max = std::max(n_max, n);
+        if ((n_max + sh.jchunk - 1) / sh.jchunk > s->part_cap_chunks) continue;
+        if (!tune) {
+            best = sh;
+            break;
+        }
+        s->dev.shape = sh;
+        GC_CUDA(launch_build_items(s->dev, s->stream));
+        float ms_sum = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            GC_CUDA(cudaMemsetAsync(&s->dev.ctrl->work_counter, 0, sizeof(unsigned), s->stream));
+            GC_CUDA(cudaEventRecord(a, s->stream));
+            GC_CUDA(launch_pair(s->dev, s->p.precision, s->p.newton, s->stream));
+            GC_CUDA(cudaEventRecord(b, s->stream));
+            GC_CUDA(cudaEventSynchronize(b));
+            float ms = 0.f;
+            GC_CUDA(cudaEventElapsedTime(&ms, a, b));
+            if (rep > 0) ms_sum += ms;  // the first launch warms up
+        }
+        if (ms_sum < best_ms) {
+            best_ms = ms_sum;
+            best = sh;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    s->dev.shape = best;
+    GC_CUDA(launch_build_items(s->dev, s->stream));
+    return GC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gc_default_params(gc_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->abi_version = GC_ABI_VERSION;
+    p->precision = GC_FP32_KAHAN;
+    p->thickness_um = 675.0;
+    p->z_well_um = 0.0;
+    p->a1_V_cm_um = 2.0;
+    p->a2_V_cm = 1500.0;
+    p->T_K = 140.0;
+    p->eps_si_rel = 11.7;
+    p->softening_um = 0.01;
+    p->dt_s = 1e-11;
+    p->max_steps = 100000;
+    p->coulomb = 1;
+    p->diffusion = 1;
+    p->reflect_back = 1;
+    p->img_w = 64;
+    p->img_h = 64;
+    p->pixel_um = 15.0;
+    p->graph_steps = 32;
+    p->autotune = 1;
+    p->newton = 0;
+    p->jchunk = 0;
+}
+
+const char *gc_status_string(gc_status st) {
+    switch (st) {
+        case GC_OK: return "GC_OK";
+        case GC_INCOMPLETE: return "GC_INCOMPLETE: max_steps reached with carriers still active";
+        case GC_ERR_PARAM: return "GC_ERR_PARAM: invalid argument or parameter";
+        case GC_ERR_ALLOC: return "GC_ERR_ALLOC: allocation failed";
+        case GC_ERR_CUDA: return "GC_ERR_CUDA: CUDA runtime error";
+        case GC_ERR_STATE: return "GC_ERR_STATE: call out of order";
+        case GC_ERR_DEVICE_TIMEOUT: return "GC_ERR_DEVICE_TIMEOUT: bounded device wait expired";
+        case GC_ERR_NO_DEVICE: return "GC_ERR_NO_DEVICE: no CUDA device";
+    }
+    return "unknown gc_status";
+}
+
+const char *gc_last_cuda_error(void) { return g_cuda_err; }
+
+gc_status gc_device_info(int32_t *sm_count, int32_t *cc_major, int32_t *cc_minor) {
+    int dev = 0, cnt = 0;
+    cudaError_t e = cudaGetDeviceCount(&cnt);
+    if (e != cudaSuccess || cnt == 0) {
+        if (e != cudaSuccess) cuda_fail(e);
+        return GC_ERR_NO_DEVICE;
+    }
+    GC_CUDA(cudaGetDevice(&dev));
+    int v = 0;
+    if (sm_count) {
+        GC_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        *sm_count = v;
+    }
+    if (cc_major) {
+        GC_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMajor, dev));
+        *cc_major = v;
+    }
+    if (cc_minor) {
+        GC_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMinor, dev));
+        *cc_minor = v;
+    }
+    return GC_OK;
+}
+
+gc_status gc_create(const gc_params *p, void *cuda_stream, gc_sim **out) {
+    if (!out) return GC_ERR_PARAM;
+    *out = nullptr;
+    gc_status v = validate(p);
+    if (v != GC_OK) return v;
+    int cnt = 0;
+    cudaError_t e = cudaGetDeviceCount(&cnt);
+    if (e != cudaSuccess || cnt == 0) {
+        if (e != cudaSuccess) cuda_fail(e);
+        return GC_ERR_NO_DEVICE;
+    }
+    gc_sim *s = new (std::nothrow) gc_sim();
+    if (!s) return GC_ERR_ALLOC;
+    s->p = *p;
+    s->phys = make_phys(*p);
+    gc_status st = GC_OK;
+    do {
+        if ((e = cudaGetDevice(&s->device)) != cudaSuccess) { st = cuda_fail(e); break; }
+        if ((e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device)) != cudaSuccess) {
+            st = cuda_fail(e);
+            break;
+        }
+        if (cuda_stream) {
+            s->stream = (cudaStream_t)cuda_stream;
+        } else {
+            if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+                st = cuda_fail(e);
+                break;
+            }
+            s->own_stream = true;
+        }
+        if ((e = cudaMallocHost((void **)&s->h_ctrl, sizeof(Ctrl))) != cudaSuccess) { st = cuda_fail(e); break; }
+        if ((e = cudaMallocHost((void **)&s->h_limit, sizeof(long long))) != cudaSuccess) { st = cuda_fail(e); break; }
+        std::memset(s->h_ctrl, 0, sizeof(Ctrl));
+    } while (0);
+    if (st != GC_OK) {
+        gc_destroy(s);
+        return st;
+    }
+    *out = s;
+    return GC_OK;
+}
+
+gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_t *event_offsets,
+                           int64_t n_events, const uint64_t *seeds, const double *img_origin_xy) {
+    if (!s) return GC_ERR_PARAM;
+    if (n < 0 || n > (1LL << 30) || (n > 0 && !xyz)) return GC_ERR_PARAM;
+    // caller's events
+    std::vector<int64_t> uoff;
+    if (event_offsets) {
+        if (n_events < 1 || n_events > (1LL << 24)) return GC_ERR_PARAM;
+        uoff.assign(event_offsets, event_offsets + n_events + 1);
+        if (uoff[0] != 0 || uoff[n_events] != n) return GC_ERR_PARAM;
+        for (int64_t e = 0; e < n_events; ++e)
+            if (uoff[e + 1] < uoff[e]) return GC_ERR_PARAM;
+    } else {
+        if (n_events > 1) return GC_ERR_PARAM;
+        n_events = 1;
+        uoff = {0, n};
+    }
+    for (int64_t i = 0; i < 3 * n; ++i)
+        if (!is_finite(xyz[i])) return GC_ERR_PARAM;
+    if (img_origin_xy)
+        for (int64_t i = 0; i < 2 * n_events; ++i)
+            if (!is_finite(img_origin_xy[i])) return GC_ERR_PARAM;
+    GC_CUDA(cudaSetDevice(s->device));
+    GC_CUDA(cudaStreamSynchronize(s->stream));
+    free_state(s);
+    const int64_t E = n_events;
+    s->n = n;
+    s->E = E;
+    s->user_off = uoff;
+
+    // internal event order: descending size (stable), i.e. largest work first
+    std::vector<int> order(E);
+    for (int64_t e = 0; e < E; ++e) order[e] = (int)e;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return uoff[a + 1] - uoff[a] > uoff[b + 1] - uoff[b];
+    });
+    std::vector<int> act(std::max<int64_t>(n, 1)), ev_of_id(std::max<int64_t>(n, 1)), ioff(E + 1);
+    std::vector<unsigned long long> eseed(E);
+    std::vector<double> eorig(3 * E), iorig(2 * E);
+    std::vector<long long> sizes(E);
+    int pos = 0;
+    for (int64_t ie = 0; ie < E; ++ie) {
+        const int ue = order[ie];
+        ioff[ie] = pos;
+        sizes[ie] = uoff[ue + 1] - uoff[ue];
+        double cx = 0, cy = 0, cz = 0;
+        for (int64_t id = uoff[ue]; id < uoff[ue + 1]; ++id) {
+            act[pos++] = (int)id;
+            ev_of_id[id] = (int)ie;
+            cx += xyz[3 * id];
+            cy += xyz[3 * id + 1];
+            cz += xyz[3 * id + 2];
+        }
+        const double cnt = (double)std::max<int64_t>(sizes[ie], 1);
+        eorig[3 * ie] = cx / cnt;
+        eorig[3 * ie + 1] = cy / cnt;
+        eorig[3 * ie + 2] = cz / cnt;
+        eseed[ie] = seeds ? (unsigned long long)seeds[ue] : 1ull;
+        if (img_origin_xy) {
+            iorig[2 * ie] = img_origin_xy[2 * ue];
+            iorig[2 * ie + 1] = img_origin_xy[2 * ue + 1];
+        } else {
+            iorig[2 * ie] = eorig[3 * ie] - 0.5 * s->p.img_w * s->p.pixel_um;
+            iorig[2 * ie + 1] = eorig[3 * ie + 1] - 0.5 * s->p.img_h * s->p.pixel_um;
+        }
+    }
+    ioff[E] = pos;
+    std::vector<int> ev_user(order.begin(), order.end());
+    std::vector<double> hx(std::max<int64_t>(n, 1)), hy(hx.size()), hz(hx.size());
+    for (int64_t i = 0; i < n; ++i) {
+        hx[i] = xyz[3 * i];
+        hy[i] = xyz[3 * i + 1];
+        hz[i] = xyz[3 * i + 2];
+    }
+
+    // partial-sum capacity: enough j-chunks for every autotune candidate
+    long long n_max = 1;
+    for (long long v : sizes) n_max = std::max(n_max, v);
+    long long cap = 1;
+    if (!fp64_mode(s) && s->phys.coulomb) {
+        for (int R : {2, 4, 8}) {
+            const int occ = std::max(1, pair_kernel_occupancy(s->p.precision, R, s->p.newton));
+            const int jc = choose_jchunk(sizes, R, 8192, s->sm_count * occ, s->p.jchunk);
+            cap = std::max(cap, (n_max + jc - 1) / jc);
+        }
+    }
+    s->part_cap_chunks = cap;
+
+    Dev &d = s->dev;
+    const size_t N = (size_t)std::max<int64_t>(n, 1);
+    const size_t nchunk = (size_t)ceil_div((int)N, kChunk);
+    const size_t img = (size_t)E * s->p.img_w * s->p.img_h;
+    DevAllocs &m = s->mem;
+    cudaError_t e = cudaSuccess;
+#define GC_ALLOC(ptr, bytes)                                                  \
+    if ((e = m.alloc((void **)&(ptr), (bytes))) != cudaSuccess) {             \
+        free_state(s);                                                        \
+        return cuda_fail(e);                                                  \
+    }
+    GC_ALLOC(d.px, N * 8) GC_ALLOC(d.py, N * 8) GC_ALLOC(d.pz, N * 8)
+    GC_ALLOC(d.ev_of_id, N * 4) GC_ALLOC(d.collect_step, N * 4)
+    GC_ALLOC(d.act[0], N * 4) GC_ALLOC(d.act[1], N * 4)
+    if (fp64_mode(s)) {
+        GC_ALLOC(d.sh64, N * sizeof(double4_32a))
+    } else {
+        GC_ALLOC(d.sh32, N * sizeof(float4))
+    }
+    if (s->phys.coulomb) {
+        GC_ALLOC(d.partial, (size_t)cap * 3 * N * 8)
+    }
+    GC_ALLOC(d.keepmask, nchunk * (kChunk / 32) * 4) GC_ALLOC(d.chunk_cnt, nchunk * 4)
+    GC_ALLOC(d.ev_off[0], (E + 1) * 4) GC_ALLOC(d.ev_off[1], (E + 1) * 4)
+    GC_ALLOC(d.ev_collected_now, E * 4) GC_ALLOC(d.item_base, (E + 1) * 4)
+    GC_ALLOC(d.ev_seed, E * 8) GC_ALLOC(d.ev_origin, E * 24) GC_ALLOC(d.img_origin, E * 16)
+    GC_ALLOC(d.ev_user, E * 4) GC_ALLOC(d.image, img * 4) GC_ALLOC(d.off_image, E * 8)
+    GC_ALLOC(d.ctrl, sizeof(Ctrl))
+#undef GC_ALLOC
+    d.part_stride = (long long)N;
+    d.n_total = (int)n;
+    d.n_events = (int)E;
+    d.phys = s->phys;
+    d.shape.R = fp64_mode(s) ? 1 : 4;
+    d.shape.small_n = fp64_mode(s) ? 0 : 8192;
+    d.shape.jchunk = round_up(n_max, kTileJ);
+    d.shape.n_blocks = s->sm_count;
+
+    cudaStream_t st = s->stream;
+    GC_CUDA(cudaMemcpyAsync(d.px, hx.data(), n * 8, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.py, hy.data(), n * 8, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.pz, hz.data(), n * 8, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.ev_of_id, ev_of_id.data(), n * 4, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.act[0], act.data(), n * 4, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.ev_off[0], ioff.data(), (E + 1) * 4, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.ev_seed, eseed.data(), E * 8, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.ev_origin, eorig.data(), E * 24, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.img_origin, iorig.data(), E * 16, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.ev_user, ev_user.data(), E * 4, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemsetAsync(d.collect_step, 0xFF, N * 4, st));
+    GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, st));
+    GC_CUDA(cudaMemsetAsync(d.image, 0, img * 4, st));
+    GC_CUDA(cudaMemsetAsync(d.off_image, 0, E * 8, st));
+    std::memset(s->h_ctrl, 0, sizeof(Ctrl));
+    s->h_ctrl->step_limit = LLONG_MAX;  // open for the step-0 pass
+    s->h_ctrl->n_active = (int)n;
+    GC_CUDA(cudaMemcpyAsync(d.ctrl, s->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+
+    s->integ_grid = std::max(1, std::min((int)nchunk, 2 * s->sm_count));
+    const bool f64 = fp64_mode(s);
+    if (n > 0) {
+        // step 0: reflect at the back surface, collect what is already in the well
+        GC_CUDA(launch_integrate(d, f64, true, s->integ_grid, st));
+        GC_CUDA(launch_compact(d, f64, s->integ_grid, st));
+        GC_CUDA(launch_finalize(d, true, st));
+    }
+    GC_CUDA(cudaStreamSynchronize(st));
+    gc_status r = read_ctrl(s);
+    if (r != GC_OK) return r;
+    if (s->phys.coulomb && n > 0) {
+        r = choose_shape(s, sizes);  // the sizes the partial buffer was sized for
+        if (r != GC_OK) return r;
+    }
+    r = set_limit(s, 0);
+    if (r != GC_OK) return r;
+    r = read_ctrl(s);
+    if (r != GC_OK) return r;
+    s->launches_per_step = (s->phys.coulomb ? 1 : 0) + 3;
+    if (s->p.timing) {
+        const int ne = std::max(1, s->p.graph_steps);
+        s->ev_a.resize(ne);
+        s->ev_b.resize(ne);
+        for (int k = 0; k < ne; ++k) {
+            GC_CUDA(cudaEventCreate(&s->ev_a[k]));
+            GC_CUDA(cudaEventCreate(&s->ev_b[k]));
+        }
+    }
+    s->loaded = true;
+    r = capture_graph(s);
+    if (r != GC_OK) {
+        s->loaded = false;
+        return r;
+    }
+    return GC_OK;
+}
+
+gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
+    if (steps_done) *steps_done = 0;
+    if (!s) return GC_ERR_PARAM;
+    if (!s->loaded) return GC_ERR_STATE;
+    GC_CUDA(cudaSetDevice(s->device));
+    const long long step0 = s->h_ctrl->step;
+    const long long max_steps = s->p.max_steps;
+    const long long limit = steps < 0 ? max_steps : std::min<long long>(max_steps, step0 + steps);
+    if (s->h_ctrl->n_active > 0 && step0 < limit) {
+        gc_status r = set_limit(s, limit);
+        if (r != GC_OK) return r;
+        const long long want = limit - step0;
+        const int K = std::max(1, s->p.graph_steps);
+        // one launch = one captured graph of K steps, or one eager step
+        auto launch_one = [&]() -> gc_status {
+            const long long before = s->h_ctrl->step;
+            if (s->p.graph_steps > 0) {
+                GC_CUDA(cudaGraphLaunch(s->graph, s->stream));
+            } else {
+                gc_status q = enqueue_step(s, 0);
+                if (q != GC_OK) return q;
+            }
+            if (s->p.timing) {  // read this launch's events before they are re-recorded
+                gc_status q = read_ctrl(s);
+                if (q != GC_OK) return q;
+                const long long did = std::min<long long>(K, s->h_ctrl->step - before);
+                for (long long k = 0; k < did && s->phys.coulomb; ++k) {
+                    float ms = 0.f;
+                    GC_CUDA(cudaEventElapsedTime(&ms, s->ev_a[k], s->ev_b[k]));
+                    s->pair_ms += ms;
+                    s->pair_launches += 1;
+                }
+            }
+            return GC_OK;
+        };
+        if (steps >= 0) {
+            // known step count: enqueue everything, synchronise once
+            for (long long k = 0; k < (want + K - 1) / K; ++k) {
+                r = launch_one();
+                if (r != GC_OK) return r;
+            }
+            r = read_ctrl(s);
+            if (r != GC_OK) return r;
+        } else {
+            // until every carrier is collected: poll between batches of steps
+            const long long batch = std::max(1, 256 / K);
+            for (;;) {
+                const long long before = s->h_ctrl->step;
+                for (long long k = 0; k < batch; ++k) {
+                    r = launch_one();
+                    if (r != GC_OK) return r;
+                }
+                r = read_ctrl(s);
+                if (r != GC_OK) return r;
+                if (s->h_ctrl->n_active <= 0 || s->h_ctrl->step >= limit) break;
+                if (s->h_ctrl->step == before) return GC_ERR_STATE;  // no progress: never spin
+            }
+        }
+        r = set_limit(s, s->h_ctrl->step);  // closed until the next gc_run
+        if (r != GC_OK) return r;
+    }
+    if (steps_done) *steps_done = s->h_ctrl->step - step0;
+    if (s->h_ctrl->n_active > 0 && s->h_ctrl->step >= max_steps) return GC_INCOMPLETE;
+    return GC_OK;
+}
+
+gc_status gc_collect(gc_sim *s, double *final_xy, int32_t *collect_step, int64_t *n_collected,
+                     int64_t *n_offimage, int64_t *n_active) {
+    if (!s) return GC_ERR_PARAM;
+    if (!s->loaded) return GC_ERR_STATE;
+    GC_CUDA(cudaSetDevice(s->device));
+    const int64_t n = s->n, E = s->E;
+    std::vector<int32_t> cs(std::max<int64_t>(n, 1));
+    GC_CUDA(cudaMemcpyAsync(cs.data(), s->dev.collect_step, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    std::vector<double> hx, hy;
+    if (final_xy) {
+        hx.resize(std::max<int64_t>(n, 1));
+        hy.resize(std::max<int64_t>(n, 1));
+        GC_CUDA(cudaMemcpyAsync(hx.data(), s->dev.px, n * 8, cudaMemcpyDeviceToHost, s->stream));
+        GC_CUDA(cudaMemcpyAsync(hy.data(), s->dev.py, n * 8, cudaMemcpyDeviceToHost, s->stream));
+    }
+    std::vector<unsigned long long> off(std::max<int64_t>(E, 1));
+    GC_CUDA(cudaMemcpyAsync(off.data(), s->dev.off_image, E * 8, cudaMemcpyDeviceToHost, s->stream));
+    GC_CUDA(cudaStreamSynchronize(s->stream));
+    if (collect_step) std::memcpy(collect_step, cs.data(), n * 4);
+    if (final_xy)
+        for (int64_t i = 0; i < n; ++i) {
+            final_xy[2 * i] = hx[i];
+            final_xy[2 * i + 1] = hy[i];
+        }
+    for (int64_t e = 0; e < E; ++e) {
+        int64_t col = 0;
+        for (int64_t i = s->user_off[e]; i < s->user_off[e + 1]; ++i) col += cs[i] >= 0;
+        if (n_collected) n_collected[e] = col;
+        if (n_active) n_active[e] = (s->user_off[e + 1] - s->user_off[e]) - col;
+        if (n_offimage) n_offimage[e] = (int64_t)off[e];
+    }
+    return GC_OK;
+}
+
+gc_status gc_image(gc_sim *s, uint32_t *img, int is_device) {
+    if (!s || !img) return GC_ERR_PARAM;
+    if (!s->loaded) return GC_ERR_STATE;
+    GC_CUDA(cudaSetDevice(s->device));
+    const size_t bytes = (size_t)s->E * s->p.img_w * s->p.img_h * 4;
+    GC_CUDA(cudaMemcpyAsync(img, s->dev.image, bytes,
+                            is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+    GC_CUDA(cudaStreamSynchronize(s->stream));
+    return GC_OK;
+}
+
+gc_status gc_positions(gc_sim *s, double *xyz) {
+    if (!s || !xyz) return GC_ERR_PARAM;
+    if (!s->loaded) return GC_ERR_STATE;
+    GC_CUDA(cudaSetDevice(s->device));
+    const int64_t n = s->n;
+    std::vector<double> hx(std::max<int64_t>(n, 1)), hy(hx.size()), hz(hx.size());
+    GC_CUDA(cudaMemcpyAsync(hx.data(), s->dev.px, n * 8, cudaMemcpyDeviceToHost, s->stream));
+    GC_CUDA(cudaMemcpyAsync(hy.data(), s->dev.py, n * 8, cudaMemcpyDeviceToHost, s->stream));
+    GC_CUDA(cudaMemcpyAsync(hz.data(), s->dev.pz, n * 8, cudaMemcpyDeviceToHost, s->stream));
+    GC_CUDA(cudaStreamSynchronize(s->stream));
+    for (int64_t i = 0; i < n; ++i) {
+        xyz[3 * i] = hx[i];
+        xyz[3 * i + 1] = hy[i];
+        xyz[3 * i + 2] = hz[i];
+    }
+    return GC_OK;
+}
+
+gc_status gc_get_stats(gc_sim *s, gc_stats *out) {
+    if (!s || !out) return GC_ERR_PARAM;
+    if (!s->loaded) return GC_ERR_STATE;
+    GC_CUDA(cudaSetDevice(s->device));
+    gc_status r = read_ctrl(s);
+    if (r != GC_OK) return r;
+    std::memset(out, 0, sizeof(*out));
+    out->steps = s->h_ctrl->step;
+    out->n_active = s->h_ctrl->n_active;
+    out->n_collected = s->n - s->h_ctrl->n_active;
+    out->pair_interactions = (double)s->h_ctrl->pair_interactions;
+    out->carrier_steps = (double)s->h_ctrl->carrier_steps;
+    out->pair_variant = s->dev.shape.R;
+    out->pair_blocks = s->dev.shape.n_blocks;
+    out->jchunk = s->dev.shape.jchunk;
+    out->launches_per_step = s->launches_per_step;
+    out->pair_kernel_ms = s->pair_ms;
+    out->pair_kernel_launches = s->pair_launches;
+    return GC_OK;
+}
+
+gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um, double eps_si_rel,
+                           int32_t precision, double *E_dev, void *cuda_stream) {
+    if (n < 0 || n > (1LL << 30)) return GC_ERR_PARAM;
+    if (!(softening_um > 0) || !is_finite(softening_um) || !(eps_si_rel > 0) || !is_finite(eps_si_rel))
+        return GC_ERR_PARAM;
+    if (precision < GC_FP64 || precision > GC_FP32_KAHAN) return GC_ERR_PARAM;
+    if (n > 0 && (!xyz_dev || !E_dev)) return GC_ERR_PARAM;
+    int cnt = 0;
+    cudaError_t e = cudaGetDeviceCount(&cnt);
+    if (e != cudaSuccess || cnt == 0) {
+        if (e != cudaSuccess) cuda_fail(e);
+        return GC_ERR_NO_DEVICE;
+    }
+    if (n == 0) return GC_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    GC_CUDA(cudaGetDevice(&dev));
+    GC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    gc_params p;
+    gc_default_params(&p);
+    p.softening_um = softening_um;
+    p.eps_si_rel = eps_si_rel;
+    Dev d{};
+    d.phys = make_phys(p);
+    const bool f64 = precision == GC_FP64;
+    std::vector<long long> sizes{n};
+    if (f64) {
+        d.shape.R = 1;
+        d.shape.small_n = 0;
+        d.shape.n_blocks = sms * std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0));
+        d.shape.jchunk = round_up(n, kTileJ);
+    } else {
+        d.shape.R = 4;
+        d.shape.small_n = 8192;
+        d.shape.n_blocks = sms * std::max(1, pair_kernel_occupancy(precision, 4, 0));
+        d.shape.jchunk = choose_jchunk(sizes, 4, 8192, d.shape.n_blocks, 0);
+    }
+    const long long S = (n + d.shape.jchunk - 1) / d.shape.jchunk;
+    DevAllocs m;
+    gc_status status = GC_OK;
+    do {
+        if ((e = m.alloc(f64 ? (void **)&d.sh64 : (void **)&d.sh32, (size_t)n * (f64 ? 32 : 16))) ||
+            (e = m.alloc((void **)&d.partial, (size_t)S * 3 * n * 8)) ||
+            (e = m.alloc((void **)&d.ev_off[0], 8)) || (e = m.alloc((void **)&d.item_base, 8)) ||
+            (e = m.alloc((void **)&d.ev_origin, 24)) || (e = m.alloc((void **)&d.ctrl, sizeof(Ctrl)))) {
+            status = cuda_fail(e);
+            break;
+        }
+        d.ev_off[1] = d.ev_off[0];
+        d.part_stride = n;
+        d.n_total = (int)n;
+        d.n_events = 1;
+        Ctrl c{};
+        c.step_limit = 1;
+        c.n_active = (int)n;
+        const int off[2] = {0, (int)n};
+        if ((e = cudaMemcpyAsync(d.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(d.ev_off[0], off, 8, cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(d.ev_origin, xyz_dev, 24, cudaMemcpyDeviceToDevice, st)) ||
+            (e = launch_field_prepare(d, xyz_dev, (int)n, f64, st)) || (e = launch_build_items(d, st)) ||
+            (e = launch_pair(d, precision, 0, st)) || (e = launch_field_finish(d, (int)n, E_dev, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            status = cuda_fail(e);
+            break;
+        }
+    } while (0);
+    cudaStreamSynchronize(st);
+    m.release();
+    return status;
+}
+
+void gc_destroy(gc_sim *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    free_state(s);
+    if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
+    if (s->h_limit) cudaFreeHost(s->h_limit);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+}  // extern "C"

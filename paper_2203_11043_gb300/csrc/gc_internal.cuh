@@ -1,0 +1,166 @@
+// gc_internal.cuh -- device-side state, physics constants and helpers shared by
+// the kernels of libgcoreccd (G-CoReCCD hole transport, arXiv 2203.11043).
+//
+// Data layout in HBM (N = carriers loaded, E = events, S = j-chunks):
+//   per carrier, by original id:  px, py, pz (FP64 SoA), ev_of_id (int32),
+//                                 collect_step (int32, -1 while active)
+//   per active slot (compacted, grouped by event, ascending id inside an
+//   event):                       act[cur] (id), sh32 (float4 shadow x,y,z
+//                                 relative to the event origin) or sh64
+//                                 (double4_32a, FP64 form), partial (FP64,
+//                                 [S][3][N]), keepmask (1 bit per slot)
+//   per event (internal order = descending initial size):
+//                                 ev_off[cur] (active offsets), item_base
+//                                 (pair work-item prefix), seeds, origins
+//   per user event:               image [E][H][W] uint32, off_image uint64
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gc {
+
+constexpr int kChunk = 4096;        // slots per integrate/compact chunk
+constexpr int kChunkThreads = 1024; // threads per integrate/compact block
+constexpr int kPairThreads = 128;   // threads per pair-kernel block
+constexpr int kTileJ = 256;         // j positions staged in shared memory per tile
+constexpr float kSentinel = 1.0e15f; // padding position: its Eq. 6 term rounds to 0
+
+// Control block: one per simulation, written only by the device during a run.
+struct Ctrl {
+    long long step;          // time steps completed
+    long long step_limit;    // stop when step reaches this (set by the host)
+    int n_active;            // active carriers at the start of the next step
+    int cur;                 // which of the double-buffered active lists is current
+    int items_total;         // pair work items for the next step
+    unsigned work_counter;   // next pair work item to hand out
+    unsigned long long carrier_steps;     // sum of active carriers over steps
+    unsigned long long pair_interactions; // sum over steps of sum_e n_e^2
+    int error;               // device-detected inconsistency (bit flags)
+    int pad;
+};
+
+// Physics and geometry, precomputed on the host from gc_params.
+struct Phys {
+    double a1, a2;           // Eq. 1
+    double thickness, z_well;
+    double dt;
+    double K;                // Eq. 6 constant, V/cm * um^2
+    double eps2;             // softening^2, um^2
+    double mu0;              // Eq. 2: 1.31e8 T^-2.2
+    double inv_Ec;           // Eq. 2: 1 / (1.24 T^1.68)
+    double beta, inv_beta;   // Eq. 2: 0.46 T^0.17 and its inverse
+    double Vth;              // k_B T / q, V (Eq. 4)
+    double pixel;            // pixel pitch, um
+    int img_w, img_h;
+    int coulomb, diffusion, reflect;
+};
+
+// Pair-kernel work decomposition, fixed at load time.
+struct PairShape {
+    int R;          // i carriers per thread (register blocking)
+    int jchunk;     // j-chunk length of a work item (multiple of kTileJ)
+    int small_n;    // events with fewer active carriers use 4 lanes per i-group
+    int n_blocks;   // persistent grid size
+};
+
+// Device view of a simulation, passed by value to every kernel.
+struct Dev {
+    double *px, *py, *pz;
+    int *ev_of_id;
+    int *collect_step;
+    int *act[2];
+    float4 *sh32;
+    double4_32a *sh64;
+    double *partial;
+    long long part_stride;
+    unsigned *keepmask;
+    int *chunk_cnt;
+    int *ev_off[2];
+    int *ev_collected_now;
+    int *item_base;
+    unsigned long long *ev_seed;
+    double *ev_origin;       // [E][3]
+    double *img_origin;      // [E][2]
+    int *ev_user;            // internal -> caller event index
+    unsigned *image;         // [E_user][H][W]
+    unsigned long long *off_image;
+    Ctrl *ctrl;
+    int n_total;
+    int n_events;
+    PairShape shape;
+    Phys phys;
+};
+
+// Number of lanes sharing one i-group in the pair kernel for an event of n
+// active carriers, and the i-tile length that follows from it.
+__host__ __device__ inline int lanes_for(int n, int small_n) { return n < small_n ? 4 : 1; }
+__host__ __device__ inline int itile_for(int R, int lanes) { return R * kPairThreads / lanes; }
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// A step is skipped when the run limit is reached or nothing is active.
+__device__ inline bool step_skipped(const Ctrl *c) {
+    return c->step >= c->step_limit || c->n_active <= 0;
+}
+
+// ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------------
+// Ten rounds of the 4x32 Philox S-box with multipliers 0xD2511F53 and
+// 0xCD9E8D57; the key advances by 0x9E3779B9 / 0xBB67AE85 between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Counter of the diffusion stream: (carrier id, step lo, step hi, 0), keyed by
+// the event seed.
+__device__ __forceinline__ uint4 diffusion_bits(unsigned long long seed, int id, long long step) {
+    return philox4x32_10(make_uint4((unsigned)id, (unsigned)step,
+                                    (unsigned)((unsigned long long)step >> 32), 0u),
+                         make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+}
+
+// ---- packed FP32 (sm_100+ f32x2) helpers -----------------------------------
+typedef unsigned long long f2;  // two FP32 lanes in one 64-bit register pair
+
+__device__ __forceinline__ f2 pack2(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// Hardware reciprocal square root on the MUFU pipe (approximate).
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+}  // namespace gc

@@ -1,0 +1,30 @@
+// gc_launch.h -- host-side launchers of libgcoreccd's kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gc_internal.cuh"
+
+namespace gc {
+
+// Pair kernel (Eq. 6): precision 0 = FP64 form, 1 = FP32, 2 = FP32 + Kahan.
+const void *pair_kernel_ptr(int precision, int R, int newton);
+int pair_kernel_occupancy(int precision, int R, int newton);
+cudaError_t launch_pair(const Dev &d, int precision, int newton, cudaStream_t st);
+
+// One time step after the pair sum: integrate (mobility, drift, diffusion,
+// update, collection, binning), compaction of the active list, and the
+// single-block bookkeeping that prepares the next step.
+cudaError_t launch_integrate(const Dev &d, bool fp64, bool init, int grid, cudaStream_t st);
+cudaError_t launch_compact(const Dev &d, bool fp64, int grid, cudaStream_t st);
+cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st);
+// Recompute the pair work items from the current active offsets (after the
+// pair-kernel shape changes).
+cudaError_t launch_build_items(const Dev &d, cudaStream_t st);
+
+// Standalone Eq. 6: FP64 [n][3] device positions -> shadow in slot order.
+cudaError_t launch_field_prepare(const Dev &d, const double *xyz, int n, bool fp64,
+                                 cudaStream_t st);
+// E[i][c] = K * sum of the chunk partials.
+cudaError_t launch_field_finish(const Dev &d, int n, double *E, cudaStream_t st);
+
+}  // namespace gc

@@ -1,0 +1,424 @@
+// step.cu -- everything in one time step after the Eq. 6 pair sum (Fig. 2):
+//
+//  integrate:  E = E_Coul + (0, 0, a1 z - a2) (Eq. 1), |E|, mu(|E|, T) (Eq. 2),
+//              v = mu E, D = mu kT/q (Eq. 4), sigma = sqrt(2 D dt) (Eq. 3),
+//              Philox-4x32-10 + Box-Muller normals, r += v dt + sigma n (FP64),
+//              reflection at the back surface, the z check (collection at
+//              z <= z_well), exact integer binning into the event's image
+//              (Fig. 5), and a warp-ballot keep mask per 32 slots.
+//  compact:    stable stream compaction of the active list (ballot masks ->
+//              popc prefix inside a 4096-slot chunk -> prefix over chunks),
+//              writing the next step's id list and FP32 / FP64 shadow.
+//  finalize:   one block: per-event active counts, new event offsets,
+//              pair work items, step and throughput counters, termination.
+//
+// No kernel waits on another block: ordering comes from the stream (or the
+// captured graph), so nothing here can spin.
+#include "gc_internal.cuh"
+#include "gc_launch.h"
+
+namespace gc {
+
+// ---- Eq. 2 mobility -------------------------------------------------------------
+__device__ __forceinline__ double mobility64(const Phys &ph, double E) {
+    return ph.mu0 / pow(1.0 + pow(E * ph.inv_Ec, ph.beta), ph.inv_beta);
+}
+__device__ __forceinline__ float mobility32(const Phys &ph, float E) {
+    const float t = exp2f((float)ph.beta * log2f(E * (float)ph.inv_Ec));
+    return (float)ph.mu0 * exp2f(-(float)ph.inv_beta * log2f(1.0f + t));
+}
+
+// ---- Box-Muller on the Philox bits (u_a in (0,1], u_b in [0,1)) ---------------------
+__device__ __forceinline__ void normals64(uint4 b, double n[3]) {
+    const double s = 2.3283064365386963e-10;  // 2^-32
+    const double r0 = sqrt(-2.0 * log(((double)b.x + 1.0) * s));
+    double sn, cs;
+    sincospi(2.0 * ((double)b.y * s), &sn, &cs);
+    n[0] = r0 * cs;
+    n[1] = r0 * sn;
+    const double r1 = sqrt(-2.0 * log(((double)b.z + 1.0) * s));
+    n[2] = r1 * cospi(2.0 * ((double)b.w * s));
+}
+__device__ __forceinline__ void normals32(uint4 b, float n[3]) {
+    const float s = 2.3283064365386963e-10f;  // 2^-32
+    const float r0 = sqrtf(-2.0f * logf(fmaf((float)b.x, s, s)));
+    float sn, cs;
+    sincospif(2.0f * ((float)b.y * s), &sn, &cs);
+    n[0] = r0 * cs;
+    n[1] = r0 * sn;
+    const float r1 = sqrtf(-2.0f * logf(fmaf((float)b.z, s, s)));
+    n[2] = r1 * cospif(2.0f * ((float)b.w * s));
+}
+
+// ---- per-slot step -------------------------------------------------------------------
+// Returns true when the carrier stays active.
+template <bool F64, bool INIT>
+__device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long long step) {
+    const Phys &ph = d.phys;
+    const int id = d.act[cur][p];
+    const int e = d.ev_of_id[id];
+    double x = d.px[id], y = d.py[id], z = d.pz[id];
+    if (INIT) {
+        if (ph.reflect && z > ph.thickness) {
+            z = 2.0 * ph.thickness - z;
+            d.pz[id] = z;
+        }
+    } else {
+        double ex = 0.0, ey = 0.0, ez = 0.0;
+        if (ph.coulomb) {  // Eq. 6: sum of the per-chunk partial sums, fixed order
+            const int *off = d.ev_off[cur];
+            const int n_e = off[e + 1] - off[e];
+            const int js = ceil_div(n_e, d.shape.jchunk);
+            const double *P = d.partial + p;
+            for (int jc = 0; jc < js; ++jc) {
+                ex += P[0];
+                ey += P[d.part_stride];
+                ez += P[2 * d.part_stride];
+                P += 3 * d.part_stride;
+            }
+            ex *= ph.K;
+            ey *= ph.K;
+            ez *= ph.K;
+        }
+        ez += ph.a1 * z - ph.a2;  // Eq. 1
+        double dx, dy, dz;
+        if (F64) {
+            const double E = sqrt(ex * ex + ey * ey + ez * ez);
+            const double mu = mobility64(ph, E);
+            const double vdt = 1e4 * mu * ph.dt;  // um per (V/cm)
+            dx = vdt * ex;
+            dy = vdt * ey;
+            dz = vdt * ez;
+            if (ph.diffusion) {
+                const double sigma = sqrt(2.0 * (1e8 * mu * ph.Vth) * ph.dt);
+                double n[3];
+                normals64(diffusion_bits(d.ev_seed[e], id, step), n);
+                dx += sigma * n[0];
+                dy += sigma * n[1];
+                dz += sigma * n[2];
+            }
+        } else {
+            const float fx = (float)ex, fy = (float)ey, fz = (float)ez;
+            const float E = sqrtf(fx * fx + fy * fy + fz * fz);
+            const float mu = mobility32(ph, E);
+            const float vdt = 1e4f * mu * (float)ph.dt;
+            float ddx = vdt * fx, ddy = vdt * fy, ddz = vdt * fz;
+            if (ph.diffusion) {
+                const float sigma = sqrtf(2.0f * (1e8f * mu * (float)ph.Vth) * (float)ph.dt);
+                float n[3];
+                normals32(diffusion_bits(d.ev_seed[e], id, step), n);
+                ddx = fmaf(sigma, n[0], ddx);
+                ddy = fmaf(sigma, n[1], ddy);
+                ddz = fmaf(sigma, n[2], ddz);
+            }
+            dx = ddx;
+            dy = ddy;
+            dz = ddz;
+        }
+        x += dx;
+        y += dy;
+        z += dz;
+        if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
+        d.px[id] = x;
+        d.py[id] = y;
+        d.pz[id] = z;
+    }
+    if (z <= ph.z_well) {  // the z check: collected at this step
+        d.collect_step[id] = (int)step;
+        const int eu = d.ev_user[e];
+        const double fx = floor((x - d.img_origin[2 * e]) / ph.pixel);
+        const double fy = floor((y - d.img_origin[2 * e + 1]) / ph.pixel);
+        if (fx >= 0.0 && fx < (double)ph.img_w && fy >= 0.0 && fy < (double)ph.img_h) {
+            const long long pix = ((long long)eu * ph.img_h + (long long)fy) * ph.img_w + (long long)fx;
+            atomicAdd(&d.image[pix], 1u);
+        } else {
+            atomicAdd(&d.off_image[eu], 1ull);
+        }
+        atomicAdd(&d.ev_collected_now[e], 1);
+        return false;
+    }
+    return true;
+}
+
+template <bool F64, bool INIT>
+__global__ void __launch_bounds__(kChunkThreads) integrate_kernel(Dev d) {
+    __shared__ int s_cnt[kChunkThreads / 32];
+    Ctrl *c = d.ctrl;
+    if (step_skipped(c)) return;
+    const int cur = c->cur;
+    const int n_act = c->n_active;
+    const long long step = INIT ? 0 : c->step + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nchunks = ceil_div(n_act, kChunk);
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        int kept = 0;
+#pragma unroll
+        for (int k = 0; k < kChunk / kChunkThreads; ++k) {
+            const int p = ch * kChunk + k * kChunkThreads + threadIdx.x;
+            const bool keep = p < n_act ? advance_slot<F64, INIT>(d, cur, p, step) : false;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) d.keepmask[p >> 5] = m;
+            kept += __popc(m);
+        }
+        if (lane == 0) s_cnt[warp] = kept;
+        __syncthreads();
+        if (warp == 0) {
+            int v = s_cnt[lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) d.chunk_cnt[ch] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- compaction ---------------------------------------------------------------------------
+template <bool F64>
+__global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
+    constexpr int WORDS = kChunk / 32;  // 128 mask words per chunk
+    __shared__ int s_wpre[WORDS];
+    __shared__ int s_wtot[WORDS / 32];
+    __shared__ int s_red[kChunkThreads / 32];
+    __shared__ int s_base;
+    Ctrl *c = d.ctrl;
+    if (step_skipped(c)) return;
+    const int cur = c->cur;
+    const int n_act = c->n_active;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int *src = d.act[cur];
+    int *dst = d.act[cur ^ 1];
+    const int nchunks = ceil_div(n_act, kChunk);
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        // kept slots in all earlier chunks
+        int acc = 0;
+        for (int k = threadIdx.x; k < ch; k += kChunkThreads) acc += d.chunk_cnt[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_red[warp] = acc;
+        // exclusive prefix of the chunk's mask-word popcounts (warps 0..3)
+        if (threadIdx.x < WORDS) {
+            const int wc = __popc(d.keepmask[(long long)ch * WORDS + threadIdx.x]);
+            int incl = wc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            s_wpre[threadIdx.x] = incl - wc;  // exclusive within the warp
+            if (lane == 31) s_wtot[warp] = incl;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int b = 0;
+            for (int w = 0; w < kChunkThreads / 32; ++w) b += s_red[w];
+            s_base = b;
+        }
+        if (threadIdx.x < WORDS && warp > 0) {
+            int add = 0;
+            for (int w = 0; w < warp; ++w) add += s_wtot[w];
+            s_wpre[threadIdx.x] += add;
+        }
+        __syncthreads();
+        const int base = s_base;
+#pragma unroll
+        for (int k = 0; k < kChunk / kChunkThreads; ++k) {
+            const int p = ch * kChunk + k * kChunkThreads + threadIdx.x;
+            const int m = k * (kChunkThreads / 32) + warp;
+            const unsigned w = d.keepmask[(long long)ch * WORDS + m];
+            if ((w >> lane) & 1u) {
+                const int q = base + s_wpre[m] + __popc(w & ((1u << lane) - 1u));
+                const int id = src[p];
+                dst[q] = id;
+                const int e = d.ev_of_id[id];
+                const double ox = d.ev_origin[3 * e], oy = d.ev_origin[3 * e + 1],
+                             oz = d.ev_origin[3 * e + 2];
+                if (F64)
+                    d.sh64[q] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
+                else
+                    d.sh32[q] = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
+                                            (float)(d.pz[id] - oz), 1.0f);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- block-wide exclusive scan (1024 threads) ------------------------------------------------
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *s_warp,
+                                                          long long &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = s_warp[lane];
+        long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        s_warp[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const long long ex = s_warp[warp] + incl - v;
+    total = s_warp[32];
+    __syncthreads();
+    return ex;
+}
+
+__device__ __forceinline__ int items_for(const Dev &d, int n) {
+    if (n <= 0 || !d.phys.coulomb) return 0;
+    const int L = lanes_for(n, d.shape.small_n);
+    return ceil_div(n, itile_for(d.shape.R, L)) * ceil_div(n, d.shape.jchunk);
+}
+
+template <bool INIT>
+__global__ void __launch_bounds__(kChunkThreads) finalize_kernel(Dev d) {
+    __shared__ long long s_warp[33];
+    Ctrl *c = d.ctrl;
+    if (step_skipped(c)) return;
+    const int cur = c->cur;
+    const int *off = d.ev_off[cur];
+    int *noff = d.ev_off[cur ^ 1];
+    long long carry_n = 0, carry_items = 0;
+    unsigned long long pairs = 0, cs = 0;
+    for (int base = 0; base < d.n_events; base += kChunkThreads) {
+        const int e = base + threadIdx.x;
+        int n_old = 0, n_new = 0;
+        if (e < d.n_events) {
+            n_old = off[e + 1] - off[e];
+            n_new = n_old - d.ev_collected_now[e];
+            d.ev_collected_now[e] = 0;
+        }
+        pairs += (unsigned long long)n_old * (unsigned long long)n_old;
+        cs += (unsigned long long)n_old;
+        long long tn, ti;
+        const long long exn = block_exclusive_scan(n_new, s_warp, tn);
+        const long long exi = block_exclusive_scan(items_for(d, n_new), s_warp, ti);
+        if (e < d.n_events) {
+            noff[e] = (int)(carry_n + exn);
+            d.item_base[e] = (int)(carry_items + exi);
+        }
+        carry_n += tn;
+        carry_items += ti;
+    }
+    // reduce the counters
+    long long dummy;
+    const long long tot_pairs_ex = block_exclusive_scan((long long)pairs, s_warp, dummy);
+    const long long tot_pairs = dummy;
+    const long long tot_cs_ex = block_exclusive_scan((long long)cs, s_warp, dummy);
+    const long long tot_cs = dummy;
+    (void)tot_pairs_ex;
+    (void)tot_cs_ex;
+    if (threadIdx.x == 0) {
+        noff[d.n_events] = (int)carry_n;
+        d.item_base[d.n_events] = (int)carry_items;
+        c->n_active = (int)carry_n;
+        c->items_total = (int)carry_items;
+        c->work_counter = 0u;
+        c->cur = cur ^ 1;
+        if (!INIT) {
+            c->step += 1;
+            c->carrier_steps += (unsigned long long)tot_cs;
+            if (d.phys.coulomb) c->pair_interactions += (unsigned long long)tot_pairs;
+        }
+    }
+}
+
+// Items only (no counters, no buffer flip): used after the pair shape changes.
+__global__ void __launch_bounds__(kChunkThreads) build_items_kernel(Dev d) {
+    __shared__ long long s_warp[33];
+    Ctrl *c = d.ctrl;
+    const int *off = d.ev_off[c->cur];
+    long long carry = 0;
+    for (int base = 0; base < d.n_events; base += kChunkThreads) {
+        const int e = base + threadIdx.x;
+        const int n = e < d.n_events ? off[e + 1] - off[e] : 0;
+        long long t;
+        const long long ex = block_exclusive_scan(items_for(d, n), s_warp, t);
+        if (e < d.n_events) d.item_base[e] = (int)(carry + ex);
+        carry += t;
+    }
+    if (threadIdx.x == 0) {
+        d.item_base[d.n_events] = (int)carry;
+        c->items_total = (int)carry;
+        c->work_counter = 0u;
+    }
+}
+
+// ---- standalone Eq. 6 helpers -------------------------------------------------------------------
+__global__ void field_prepare_kernel(Dev d, const double *__restrict__ xyz, int n, bool f64) {
+    const double ox = d.ev_origin[0], oy = d.ev_origin[1], oz = d.ev_origin[2];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double x = xyz[3LL * i] - ox, y = xyz[3LL * i + 1] - oy, z = xyz[3LL * i + 2] - oz;
+        if (f64) d.sh64[i] = make_double4_32a(x, y, z, 0.0);
+        else d.sh32[i] = make_float4((float)x, (float)y, (float)z, 1.0f);
+    }
+}
+
+__global__ void field_finish_kernel(Dev d, int n, double *__restrict__ E) {
+    const int js = ceil_div(n, d.shape.jchunk);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double ex = 0.0, ey = 0.0, ez = 0.0;
+        const double *P = d.partial + i;
+        for (int jc = 0; jc < js; ++jc) {
+            ex += P[0];
+            ey += P[d.part_stride];
+            ez += P[2 * d.part_stride];
+            P += 3 * d.part_stride;
+        }
+        E[3LL * i] = d.phys.K * ex;
+        E[3LL * i + 1] = d.phys.K * ey;
+        E[3LL * i + 2] = d.phys.K * ez;
+    }
+}
+
+// ---- launchers ---------------------------------------------------------------------------------------
+cudaError_t launch_integrate(const Dev &d, bool fp64, bool init, int grid, cudaStream_t st) {
+    if (fp64) {
+        if (init) integrate_kernel<true, true><<<grid, kChunkThreads, 0, st>>>(d);
+        else integrate_kernel<true, false><<<grid, kChunkThreads, 0, st>>>(d);
+    } else {
+        if (init) integrate_kernel<false, true><<<grid, kChunkThreads, 0, st>>>(d);
+        else integrate_kernel<false, false><<<grid, kChunkThreads, 0, st>>>(d);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Dev &d, bool fp64, int grid, cudaStream_t st) {
+    if (fp64) compact_kernel<true><<<grid, kChunkThreads, 0, st>>>(d);
+    else compact_kernel<false><<<grid, kChunkThreads, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st) {
+    if (init) finalize_kernel<true><<<1, kChunkThreads, 0, st>>>(d);
+    else finalize_kernel<false><<<1, kChunkThreads, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_items(const Dev &d, cudaStream_t st) {
+    build_items_kernel<<<1, kChunkThreads, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_prepare(const Dev &d, const double *xyz, int n, bool fp64, cudaStream_t st) {
+    const int grid = n > 0 ? min(ceil_div(n, 256), 4096) : 1;
+    field_prepare_kernel<<<grid, 256, 0, st>>>(d, xyz, n, fp64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_finish(const Dev &d, int n, double *E, cudaStream_t st) {
+    const int grid = n > 0 ? min(ceil_div(n, 256), 4096) : 1;
+    field_finish_kernel<<<grid, 256, 0, st>>>(d, n, E);
+    return cudaGetLastError();
+}
+
+}  // namespace gc

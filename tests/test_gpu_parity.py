@@ -1,0 +1,314 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances:
+  * FP64 form: carrier counts, collection steps and images bit-exact; final
+    positions within 1e-4 um; the Eq. 6 field within 1e-12 of sum_j |term_j|.
+  * FP32 forms: the Eq. 6 field within an error bound derived from FP32
+    arithmetic (unit roundoff u = 2^-24): per term ~12 u from the operations
+    plus the rounding of the FP32 shadow positions (|coordinate| <= rho
+    relative to the event origin) amplified by 1/sqrt(d^2 + eps^2); the sum
+    adds (tile length + 16) u of sum_j |term_j| with Kahan across tiles, or
+    (n + 16) u without it.
+  * FP32 full runs: collected totals exact; sigma_x, sigma_y of the final
+    positions within 0.5 % of the oracle's; image L1 difference <= 1 % of the
+    charge (the acceptance bar of the method's reduced-precision forms).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2203_11043_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+TILE_J = 256
+
+
+@pytest.fixture(scope="module")
+def gc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11043_gb300 import build
+    build.build()
+    import paper_2203_11043_gb300 as g
+    g.load()
+    return g
+
+
+def gpu_field(gc, xyz, precision, eps=0.01):
+    import torch
+    t = torch.tensor(np.ascontiguousarray(xyz), dtype=torch.float64, device="cuda")
+    E = torch.full_like(t, float("nan"))
+    gc.gc_coulomb_field(t, len(xyz), eps, 11.7, precision, E, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return E.cpu().numpy()
+
+
+def field_bound(xyz, targets, precision, eps=0.01):
+    """Per-target, per-component error bound of the GPU Eq. 6 sum."""
+    K = O.coulomb_K(11.7)
+    rho = np.abs(xyz - xyz[0]).max()
+    n = len(xyz)
+    out = np.zeros((len(targets), 3))
+    for k, i in enumerate(targets):
+        d = xyz[i] - xyz
+        s2 = (d * d).sum(1) + eps * eps
+        mag = np.sqrt((d * d).sum(1)) / s2 ** 1.5
+        if precision == 0:
+            out[k] = 1e-12 * K * mag.sum() + 1e-300
+            continue
+        acc = (TILE_J + 16) if precision == 2 else (n + 16)
+        per = mag * (12 * U32 + 20 * U32 * rho / np.sqrt(s2))
+        out[k] = K * (per.sum() + acc * U32 * mag.sum())
+    return out
+
+
+def cloud(n, seed, sigma=0.5, z=300.0):
+    rng = np.random.default_rng(seed)
+    return np.array([0.0, 0.0, z]) + sigma * rng.standard_normal((n, 3))
+
+
+# ---- Eq. 6 on its own -------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 2, 7, 300, 2000, 9000])
+def test_field_matches_oracle_within_bound(gc, precision, n):
+    xyz = cloud(n, seed=n)
+    E = gpu_field(gc, xyz, precision)
+    ref = O.coulomb_field(xyz)
+    tg = np.unique(np.concatenate([np.arange(min(n, 64)), np.arange(max(0, n - 64), n)]))
+    assert np.all(np.isfinite(E))
+    bound = field_bound(xyz, tg, precision)
+    err = np.abs(E[tg] - ref[tg])
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_field_two_body_and_antisymmetry(gc):
+    K = O.coulomb_K(11.7)
+    xyz = np.array([[0.0, 0.0, 10.0], [0.3, 0.0, 10.0]])
+    for prec in (0, 2):
+        E = gpu_field(gc, xyz, prec)
+        mag = K * 0.3 / (0.09 + 1e-4) ** 1.5
+        np.testing.assert_allclose(E, [[-mag, 0, 0], [mag, 0, 0]], rtol=1e-6 if prec else 1e-13,
+                                   atol=1e-9 * mag)
+    xyz = cloud(3000, seed=4)
+    E = gpu_field(gc, xyz, 0)
+    assert np.abs(E.sum(0)).max() <= 1e-11 * np.abs(E).sum()
+
+
+def test_field_is_deterministic(gc):
+    xyz = cloud(5000, seed=8)
+    a = gpu_field(gc, xyz, 2)
+    b = gpu_field(gc, xyz, 2)
+    assert np.array_equal(a, b)
+
+
+# ---- full runs ----------------------------------------------------------------------------------
+
+def run_gpu(gc, wl, precision, **kw):
+    p = gc.gc_default_params(precision=precision, img_w=wl.img_w, img_h=wl.img_h, **kw)
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+        st, steps = sim.run(-1)
+        res = sim.collect()
+        res["image"] = sim.image()
+        res["positions"] = sim.positions()
+        res["status"], res["steps"] = st, steps
+        res["stats"] = sim.stats()
+    return res
+
+
+def run_oracle(wl, **kw):
+    ref = O.Simulation(O.make_params(img_w=wl.img_w, img_h=wl.img_h, **kw), wl.xyz, wl.ev_off,
+                       wl.seeds, wl.img_origin)
+    ref.run()
+    return ref
+
+
+def assert_fp64_parity(res, ref, wl):
+    assert res["status"] == 0
+    assert res["steps"] == ref.step
+    assert np.array_equal(res["collect_step"], ref.collect_step)
+    assert np.array_equal(res["image"], ref.image)
+    assert np.array_equal(res["n_offimage"], ref.off_image)
+    assert np.array_equal(res["n_active"], ref.n_active())
+    sizes = np.diff(wl.ev_off)
+    assert np.array_equal(res["n_collected"] + res["n_active"], sizes)
+    err = np.abs(res["positions"] - ref.positions()).max() if wl.n else 0.0
+    assert err <= 1e-4, err
+    return err
+
+
+def test_fp64_single_cloud_n256(gc):
+    """N = 256, sigma 0.5 um at z0 = 300 um, 32 x 32 image, to completion."""
+    wl = I.single_cloud()
+    res = run_gpu(gc, wl, 0)
+    ref = run_oracle(wl)
+    err = assert_fp64_parity(res, ref, wl)
+    assert err < 1e-9
+    st = res["stats"]
+    assert st["n_active"] == 0 and st["steps"] == ref.step
+    # pair interactions counted on the device equal sum over steps of N_active^2
+    cs = ref.collect_step
+    active_per_step = [(cs >= s).sum() + (cs < 0).sum() for s in range(1, ref.step + 1)]
+    assert st["pair_interactions"] == float(sum(a * a for a in active_per_step))
+    assert st["carrier_steps"] == float(sum(active_per_step))
+
+
+def test_fp64_xray_5p9kev_n1573(gc):
+    """5.9 keV X-ray, N = 1573, sigma 0.3 um, 64 x 64 image, to completion."""
+    wl = I.xray_5p9kev()
+    res = run_gpu(gc, wl, 0)
+    ref = run_oracle(wl, img_w=64, img_h=64)
+    assert_fp64_parity(res, ref, wl)
+
+
+def ragged_batch():
+    """Events of uneven size, incl. an empty one, a single carrier, one whose
+    carriers all start in the well and one that starts beyond the back."""
+    rng = np.random.default_rng(21)
+    parts, sizes = [], []
+    spec = [(70, 3.0), (0, 5.0), (1, 4.0), (300, 6.0), (33, -2.0), (5, 676.0), (130, 2.0)]
+    for n, z in spec:
+        parts.append(rng.normal(size=(n, 3)) * 0.4 + np.array([0, 0, z]))
+        sizes.append(n)
+    xyz = np.concatenate(parts)
+    ev = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    E = len(sizes)
+    origin = np.tile([[-8.0, -8.0]], (E, 1))
+    return I.Workload("ragged", xyz, ev, np.arange(11, 11 + E, dtype=np.uint64), origin, 16, 16)
+
+
+@pytest.mark.parametrize("graph_steps", [0, 8])
+def test_fp64_ragged_batch(gc, graph_steps):
+    wl = ragged_batch()
+    kw = dict(pixel_um=1.0)
+    res = run_gpu(gc, wl, 0, pixel_um=1.0, graph_steps=graph_steps)
+    ref = run_oracle(wl, **kw)
+    assert_fp64_parity(res, ref, wl)
+
+
+def test_coulomb_off_diffusion_matches_oracle(gc):
+    """Coulomb off: the diffusion normals (Philox + Box-Muller) and the drift
+    agree with the oracle's to FP64 rounding, so every collection step and
+    pixel agrees."""
+    wl = I.single_cloud(n=4000, sigma_um=0.5, z0_um=80.0, seed=5, img=32)
+    res = run_gpu(gc, wl, 0, coulomb=0)
+    ref = run_oracle(wl, coulomb=0)
+    err = assert_fp64_parity(res, ref, wl)
+    assert err < 1e-9
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fp32_xray_statistics(gc, precision):
+    """FP32 pair sum on the 5.9 keV cloud: collected totals exact, sigma_x and
+    sigma_y within 0.5 %, image L1 difference <= 1 % of the charge."""
+    wl = I.xray_5p9kev()
+    res = run_gpu(gc, wl, precision)
+    ref = run_oracle(wl, img_w=64, img_h=64)
+    assert res["status"] == 0
+    assert res["n_collected"][0] == ref.n - ref.n_active()[0] == wl.n
+    pos, rp = res["positions"], ref.positions()
+    for c in (0, 1):
+        assert pos[:, c].std() == pytest.approx(rp[:, c].std(), rel=5e-3)
+    l1 = np.abs(res["image"].astype(np.int64) - ref.image.astype(np.int64)).sum()
+    assert l1 <= 0.01 * wl.n
+    assert int(res["image"].sum()) + int(res["n_offimage"][0]) == wl.n
+
+
+def test_graph_equals_eager_and_split_runs(gc):
+    """Graph-captured and eager launches, and a run split in pieces, give
+    bit-identical results (the pipeline is deterministic)."""
+    wl = I.single_cloud(n=700, sigma_um=0.4, z0_um=60.0, seed=9, img=32)
+    outs = []
+    for gs, pieces in [(0, [-1]), (16, [-1]), (5, [3, 40, 1, -1])]:
+        p = gc.gc_default_params(precision=2, img_w=32, img_h=32, graph_steps=gs)
+        with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+            done = 0
+            for k in pieces:
+                done += sim.run(k)[1]
+            outs.append((done, sim.positions(), sim.collect()["collect_step"], sim.image()))
+    for o in outs[1:]:
+        assert o[0] == outs[0][0]
+        assert np.array_equal(o[1], outs[0][1])
+        assert np.array_equal(o[2], outs[0][2])
+        assert np.array_equal(o[3], outs[0][3])
+
+
+def test_max_steps_incomplete_and_counts(gc):
+    wl = I.single_cloud(n=200, z0_um=300.0)
+    p = gc.gc_default_params(precision=2, img_w=32, img_h=32, max_steps=100)
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+        st, steps = sim.run(-1)
+        assert st == gc.GC_INCOMPLETE and steps == 100
+        st, steps = sim.run(10)
+        assert st == gc.GC_INCOMPLETE and steps == 0
+        r = sim.collect()
+        assert r["n_active"][0] + r["n_collected"][0] == 200
+        assert np.all(r["collect_step"] == -1)
+
+
+def test_edge_cases(gc):
+    # no carriers
+    p = gc.gc_default_params(img_w=8, img_h=8)
+    with gc.Simulation(p, np.zeros((0, 3))) as sim:
+        assert sim.run(-1) == (gc.GC_OK, 0)
+        assert sim.image().sum() == 0
+    # every carrier already in the well: collected at step 0
+    xyz = np.array([[0.0, 0.0, -1.0], [1.0, 2.0, 0.0], [5.0, 5.0, -3.0]])
+    with gc.Simulation(gc.gc_default_params(img_w=8, img_h=8), xyz, img_origin=[[-60.0, -60.0]]) as sim:
+        assert sim.run(-1) == (gc.GC_OK, 0)
+        r = sim.collect()
+        assert np.all(r["collect_step"] == 0)
+        np.testing.assert_array_equal(r["final_xy"], xyz[:, :2])
+        assert sim.image().sum() == 3
+    # out-of-order call
+    h = gc.gc_create(gc.gc_default_params())
+    try:
+        with pytest.raises(gc.GcError):
+            gc.gc_run(h, 1)
+    finally:
+        gc.gc_destroy(h)
+    # inconsistent event offsets
+    h = gc.gc_create(gc.gc_default_params())
+    try:
+        with pytest.raises(gc.GcError):
+            gc.gc_load_carriers(h, np.zeros((4, 3)) + 5, event_offsets=[0, 3, 2, 4])
+    finally:
+        gc.gc_destroy(h)
+
+
+# ---- full-size sampled checks (the benchmark's workload and launch shape) ------------------------
+
+@pytest.mark.parametrize("which", ["bundle", "muon"])
+def test_large_field_sampled(gc, which):
+    """Eq. 6 at 1,048,576 carriers (16 tracks) and 200,000 (one muon track),
+    FP32 + Kahan, checked on sampled carriers against the oracle."""
+    wl = I.track_bundle() if which == "bundle" else I.muon_track()
+    E = gpu_field(gc, wl.xyz, 2)
+    rng = np.random.default_rng(1)
+    tg = np.sort(rng.choice(wl.n, size=48, replace=False))
+    ref = O.coulomb_field(wl.xyz, targets=tg)
+    bound = field_bound(wl.xyz, tg, 2)
+    err = np.abs(E[tg] - ref)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_large_one_step_sampled(gc):
+    """One full step at 1,048,576 carriers through gc_run, sampled carriers
+    against the oracle's step for the same carriers."""
+    wl = I.track_bundle()
+    p = gc.gc_default_params(precision=2, img_w=512, img_h=512)
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+        x0 = sim.positions()
+        cs0 = sim.collect()["collect_step"]
+        st, steps = sim.run(1)
+        assert steps == 1
+        x1 = sim.positions()
+    active = np.nonzero(cs0 < 0)[0]
+    rng = np.random.default_rng(2)
+    tg = np.sort(rng.choice(active, size=48, replace=False))
+    want = O.step_targets(O.make_params(img_w=512, img_h=512), x0, active, tg, int(wl.seeds[0]), 1)
+    err = np.abs(x1[tg] - want).max()
+    assert err < 1e-4, err
