@@ -80,7 +80,8 @@ typedef struct {
     int32_t newton;        /* 1: one Newton step after the MUFU rsqrt (FP32 forms) */
     int32_t jchunk;        /* j-chunk length of a pair work item; 0 = automatic */
     int32_t pair_R;        /* carriers per thread in the FP32 pair kernel (2, 4, 8); 0 = automatic */
-    int32_t timing;        /* 1: bracket every pair-kernel launch with CUDA events (gc_get_stats) */
+    int32_t timing;        /* 1: bracket every pair-kernel launch with CUDA events (gc_get_stats);
+                              steps are then launched one by one instead of as graphs */
 } gc_params;
 
 typedef struct gc_sim gc_sim;

@@ -153,6 +153,9 @@ struct gc_sim {
 namespace {
 
 bool fp64_mode(const gc_sim *s) { return s->p.precision == GC_FP64; }
+// Timing mode launches eagerly: events recorded by captured graph nodes
+// cannot be used with cudaEventElapsedTime.
+bool use_graph(const gc_sim *s) { return s->p.graph_steps > 0 && !s->p.timing; }
 
 void free_state(gc_sim *s) {
     if (s->graph) {
@@ -202,7 +205,7 @@ gc_status capture_graph(gc_sim *s) {
         cudaGraphExecDestroy(s->graph);
         s->graph = nullptr;
     }
-    if (s->p.graph_steps <= 0) return GC_OK;
+    if (!use_graph(s)) return GC_OK;
     cudaGraph_t g = nullptr;
     GC_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     gc_status st = GC_OK;
@@ -563,7 +566,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     if (r != GC_OK) return r;
     s->launches_per_step = (s->phys.coulomb ? 1 : 0) + 3;
     if (s->p.timing) {
-        const int ne = std::max(1, s->p.graph_steps);
+        const int ne = 1;
         s->ev_a.resize(ne);
         s->ev_b.resize(ne);
         for (int k = 0; k < ne; ++k) {
@@ -592,11 +595,11 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
         gc_status r = set_limit(s, limit);
         if (r != GC_OK) return r;
         const long long want = limit - step0;
-        const int K = std::max(1, s->p.graph_steps);
+        const int K = use_graph(s) ? s->p.graph_steps : 1;
         // one launch = one captured graph of K steps, or one eager step
         auto launch_one = [&]() -> gc_status {
             const long long before = s->h_ctrl->step;
-            if (s->p.graph_steps > 0) {
+            if (use_graph(s)) {
                 GC_CUDA(cudaGraphLaunch(s->graph, s->stream));
             } else {
                 gc_status q = enqueue_step(s, 0);

@@ -160,7 +160,7 @@ def test_fp64_xray_5p9kev_n1573(gc):
     """5.9 keV X-ray, N = 1573, sigma 0.3 um, 64 x 64 image, to completion."""
     wl = I.xray_5p9kev()
     res = run_gpu(gc, wl, 0)
-    ref = run_oracle(wl, img_w=64, img_h=64)
+    ref = run_oracle(wl)
     assert_fp64_parity(res, ref, wl)
 
 
@@ -206,7 +206,7 @@ def test_fp32_xray_statistics(gc, precision):
     sigma_y within 0.5 %, image L1 difference <= 1 % of the charge."""
     wl = I.xray_5p9kev()
     res = run_gpu(gc, wl, precision)
-    ref = run_oracle(wl, img_w=64, img_h=64)
+    ref = run_oracle(wl)
     assert res["status"] == 0
     assert res["n_collected"][0] == ref.n - ref.n_active()[0] == wl.n
     pos, rp = res["positions"], ref.positions()
@@ -312,3 +312,21 @@ def test_large_one_step_sampled(gc):
     want = O.step_targets(O.make_params(img_w=512, img_h=512), x0, active, tg, int(wl.seeds[0]), 1)
     err = np.abs(x1[tg] - want).max()
     assert err < 1e-4, err
+
+
+def test_timing_mode_counts_pair_launches(gc):
+    """timing = 1 brackets each pair launch with CUDA events; results are the
+    same as the graph-launched run."""
+    wl = I.single_cloud(n=3000, sigma_um=0.5, z0_um=200.0, seed=12, img=32)
+    outs = []
+    for timing in (0, 1):
+        p = gc.gc_default_params(precision=2, img_w=32, img_h=32, graph_steps=4, timing=timing)
+        with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+            sim.run(7)
+            st = sim.stats()
+            outs.append(sim.positions())
+        if timing:
+            assert st["pair_kernel_launches"] == 7 and st["pair_kernel_ms"] > 0
+        else:
+            assert st["pair_kernel_launches"] == 0
+    assert np.array_equal(outs[0], outs[1])
