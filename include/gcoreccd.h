@@ -162,6 +162,28 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
                            double eps_si_rel, int32_t precision, double *E_dev,
                            void *cuda_stream);
 
+/* Largest n accepted by gc_coulomb_field_noalloc. */
+#define GC_NOALLOC_MAX_CARRIERS 32768
+
+/* gc_coulomb_field for callers that cannot allocate device memory: code
+ * running inside an allocator or memory pool it must not re-enter, inside a
+ * framework that owns every device byte, or after a start-up phase beyond
+ * which allocation is not allowed.  Same arguments, units, layout and result
+ * (up to the order of FP32 rounding) as gc_coulomb_field; the paper has no
+ * counterpart of this entry point.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine: its scratch (about 4.2 MB) is a fixed device array
+ * inside the library, held by every GPU that loads it until the process
+ * exits.  n above GC_NOALLOC_MAX_CARRIERS returns GC_ERR_PARAM.  The first
+ * call on each device looks up that array's device address (with the device
+ * current), so make that first call before any stream capture.  Every call
+ * shares the array and finds the previous call's contents there; the call
+ * resets what must start from zero, but calls whose work overlaps on the GPU
+ * (other streams or host threads) race and must be serialised by the caller.
+ * Returns after the device has finished. */
+gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, double softening_um,
+                                   double eps_si_rel, int32_t precision, double *E_dev,
+                                   void *cuda_stream);
+
 /* Free everything owned by the simulation (NULL is a no-op). */
 void gc_destroy(gc_sim *s);
 

@@ -1,6 +1,6 @@
 """Build libgcoreccd.so in-tree with nvcc for sm_103a (GB300).
 
-The three translation units compile in parallel; the result is
+The translation units compile in parallel; the result is
 paper_2203_11043_gb300/lib/libgcoreccd.so (static CUDA runtime, C ABI only).
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libgcoreccd.so")
-SOURCES = ["pair.cu", "step.cu", "api.cu"]
+SOURCES = ["pair.cu", "step.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -24,7 +24,8 @@ GC_FP64, GC_FP32, GC_FP32_KAHAN, GC_FP16X2 = 0, 1, 2, 3
 
 # Every symbol include/gcoreccd.h declares.
 EXPORTS = ("gc_default_params", "gc_create", "gc_load_carriers", "gc_run", "gc_collect",
-           "gc_image", "gc_positions", "gc_get_stats", "gc_coulomb_field", "gc_destroy",
+           "gc_image", "gc_positions", "gc_get_stats", "gc_coulomb_field",
+           "gc_coulomb_field_noalloc", "gc_destroy",
            "gc_status_string", "gc_last_cuda_error", "gc_device_info")
 
 
@@ -118,6 +119,8 @@ def load():
         L.gc_get_stats.argtypes = [P, ctypes.POINTER(GcStats)]
         L.gc_coulomb_field.restype = I32
         L.gc_coulomb_field.argtypes = [P, I64, ctypes.c_double, ctypes.c_double, I32, P, P]
+        L.gc_coulomb_field_noalloc.restype = I32
+        L.gc_coulomb_field_noalloc.argtypes = [P, I64, ctypes.c_double, ctypes.c_double, I32, P, P]
         L.gc_destroy.restype = None
         L.gc_destroy.argtypes = [P]
         L.gc_status_string.restype = ctypes.c_char_p
@@ -240,6 +243,19 @@ def gc_coulomb_field(xyz_dev, n: int, softening_um: float, eps_si_rel: float, pr
     s = None if stream is None else ctypes.c_void_p(int(stream))
     _check(load().gc_coulomb_field(_dev_ptr(xyz_dev), int(n), float(softening_um), float(eps_si_rel),
                                    int(precision), _dev_ptr(E_dev), s), "gc_coulomb_field")
+
+
+GC_NOALLOC_MAX_CARRIERS = 32768
+
+
+def gc_coulomb_field_noalloc(xyz_dev, n: int, softening_um: float, eps_si_rel: float, precision: int,
+                             E_dev, stream=None) -> None:
+    """gc_coulomb_field without any device allocation (n <= GC_NOALLOC_MAX_CARRIERS);
+    for callers that may not allocate.  Calls must not overlap on the GPU."""
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load().gc_coulomb_field_noalloc(_dev_ptr(xyz_dev), int(n), float(softening_um),
+                                           float(eps_si_rel), int(precision), _dev_ptr(E_dev), s),
+           "gc_coulomb_field_noalloc")
 
 
 def gc_destroy(sim) -> None:
