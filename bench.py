@@ -177,6 +177,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-carriers", type=int, default=0,
+                    help="run on a random sub-sample of the bundle (profiling small cases)")
+    ap.add_argument("--pair-R", type=int, default=0, help="force the pair-kernel register blocking")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -197,11 +200,13 @@ def main():
     sms, ccmaj, ccmin = gc.gc_device_info()
 
     wl = inputs.track_bundle()
+    if args.n_carriers:
+        wl = inputs.subsample(wl, args.n_carriers, seed=3)
     # every rank runs an independent replica of the event (replicas only: the
     # single event is not sharded); seeds differ per rank
     seeds = wl.seeds + np.uint64(rank)
     params = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
-                                  graph_steps=1, timing=1)
+                                  graph_steps=1, timing=1, pair_R=args.pair_R)
     sim = gc.Simulation(params, wl.xyz, wl.ev_off, seeds, wl.img_origin, stream=stream.cuda_stream)
     st0 = sim.stats()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

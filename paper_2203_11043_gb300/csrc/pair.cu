@@ -10,11 +10,13 @@
 //    event, events by descending size (largest first), so thousands of
 //    uneven events share one launch and one big event splits into
 //    equal-cost items;
-//  * each thread keeps R i-carriers in registers as R/2 packed FP32 pairs
-//    and runs every step of the pair term on the f32x2 pipe path
-//    (sub/fma/mul .f32x2), with the reciprocal square root on MUFU;
-//  * j positions are staged in shared memory pre-duplicated as {x,x},{y,y},
-//    {z,z} so one broadcast load feeds R/2 packed pairs;
+//  * each thread keeps R i-carriers in registers, each duplicated as a
+//    packed FP32 pair {x_i, x_i}, and pairs it with two j's at a time: every
+//    step of the pair term runs as packed f32x2 instructions
+//    (sub/fma/mul .f32x2) with the reciprocal square root on MUFU;
+//  * j positions are staged in shared memory as SoA tiles, so one 16-byte
+//    broadcast load per coordinate feeds four j's (two packed pairs) to
+//    every i of the thread;
 //  * per-tile FP32 sums are folded into Kahan-compensated running sums
 //    (FP32_KAHAN), and each item writes an FP64 partial per j-chunk; the
 //    integrate kernel adds the chunks in a fixed order (deterministic);
@@ -27,16 +29,23 @@
 namespace gc {
 
 // ---------------------------------------------------------------------------
-// FP32 work item.  L lanes share one i-group; each thread owns R carriers.
+// FP32 work item, packed over j: each thread owns R i-carriers, each held
+// duplicated as {x_i, x_i}; the shared tile is SoA (x[], y[], z[]) so one
+// 16-byte load per coordinate brings four consecutive j's as two packed pairs
+// {x_j, x_j+1}.  Each packed accumulator holds the even-j and odd-j sums of
+// one i; the Kahan state of the cross-tile sums stays in registers.  L lanes
+// share an i-group and split the j range.
 template <int R, bool KAHAN, bool NEWTON, int L>
-__device__ __forceinline__ void pair_item_fp32(const Dev &d, int e_start, int n_e, int local,
-                                               ulonglong2 *__restrict__ s_xy,
-                                               f2 *__restrict__ s_z) {
-    constexpr int Q = R / 2;
-    constexpr int G = 32 / L;                 // i-groups per warp
-    constexpr int STRIDE = kPairThreads / L;  // distance between a thread's carriers
-    constexpr int IB = R * STRIDE;            // carriers per i-tile
-    constexpr int PER = kTileJ / kPairThreads;
+__device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int n_e, int local,
+                                                 float *__restrict__ sx, float *__restrict__ sy,
+                                                 float *__restrict__ sz) {
+    constexpr int G = 32 / L;
+    constexpr int STRIDE = kPairThreads / L;
+    constexpr int IB = R * STRIDE;
+    constexpr int TJ = kTileJ;               // j positions per shared-memory tile
+    constexpr int PER = TJ / kPairThreads;
+    constexpr int JU = 2;             // 16-byte loads (4 j's) per coordinate per iteration
+    constexpr int STEP = 4 * JU * L;  // j's consumed per unrolled iteration by the L lanes
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane / L, ph = lane % L;
     const int jchunk = d.shape.jchunk;
@@ -44,27 +53,25 @@ __device__ __forceinline__ void pair_item_fp32(const Dev &d, int e_start, int n_
     const int it = local / js, jc = local - it * js;
     const int il0 = it * IB + warp * G + g;
 
-    f2 xi[Q], yi[Q], zi[Q];
+    f2 xi[R], yi[R], zi[R], ax[R], ay[R], az[R];
+    const f2 ZERO = pack2(0.f, 0.f);
+    f2 kreg[KAHAN ? 6 * R : 1];  // Kahan sums and compensations, {even, odd} j
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        float4 a = make_float4(kSentinel, kSentinel, kSentinel, 0.f), b = a;
-        const int ia = il0 + (2 * q) * STRIDE, ib = il0 + (2 * q + 1) * STRIDE;
+    for (int r = 0; r < R; ++r) {
+        float4 a = make_float4(kSentinel, kSentinel, kSentinel, 0.f);
+        const int ia = il0 + r * STRIDE;
         if (ia < n_e) a = d.sh32[e_start + ia];
-        if (ib < n_e) b = d.sh32[e_start + ib];
-        xi[q] = pack2(a.x, b.x);
-        yi[q] = pack2(a.y, b.y);
-        zi[q] = pack2(a.z, b.z);
+        xi[r] = pack2(a.x, a.x);
+        yi[r] = pack2(a.y, a.y);
+        zi[r] = pack2(a.z, a.z);
+        ax[r] = ay[r] = az[r] = ZERO;
+        if (KAHAN) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) kreg[r * 6 + c] = ZERO;
+        }
     }
     const float eps2f = (float)d.phys.eps2;
     const f2 EPS2 = pack2(eps2f, eps2f);
-    const f2 ZERO = pack2(0.f, 0.f);
-    f2 ax[Q], ay[Q], az[Q], sx[Q], sy[Q], sz[Q], cx[Q], cy[Q], cz[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        ax[q] = ay[q] = az[q] = ZERO;
-        sx[q] = sy[q] = sz[q] = ZERO;
-        cx[q] = cy[q] = cz[q] = ZERO;
-    }
 
     const int j0 = jc * jchunk;
     const int j1 = min(n_e, j0 + jchunk);
@@ -77,92 +84,95 @@ __device__ __forceinline__ void pair_item_fp32(const Dev &d, int e_start, int n_
         }
     };
     fetch(j0);
-    for (int jt = j0; jt < j1; jt += kTileJ) {
+    for (int jt = j0; jt < j1; jt += TJ) {
         __syncthreads();  // the previous tile has been consumed
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int k = u * kPairThreads + tid;
-            s_xy[k] = make_ulonglong2(pack2(pre[u].x, pre[u].x), pack2(pre[u].y, pre[u].y));
-            s_z[k] = pack2(pre[u].z, pre[u].z);
+            sx[k] = pre[u].x;
+            sy[k] = pre[u].y;
+            sz[k] = pre[u].z;
         }
         __syncthreads();
-        const int cnt = min(kTileJ, j1 - jt);
-        if (jt + kTileJ < j1) fetch(jt + kTileJ);  // overlaps the loads with this tile's work
-        const int kmax = (cnt + 4 * L - 1) / (4 * L) * (4 * L);  // padded with sentinels
-        for (int k0 = 0; k0 < kmax; k0 += 4 * L) {
+        const int cnt = min(TJ, j1 - jt);
+        if (jt + TJ < j1) fetch(jt + TJ);  // overlaps the loads with this tile's work
+        const int kmax = (cnt + STEP - 1) / STEP * STEP;  // padded with sentinels
+        for (int k0 = 4 * ph; k0 < kmax; k0 += STEP) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = k0 + u * L + ph;
-                const ulonglong2 xy = s_xy[k];
-                const f2 zz = s_z[k];
+            for (int u = 0; u < JU; ++u) {
+                const int k = k0 + u * 4 * L;
+                const ulonglong2 X = *reinterpret_cast<const ulonglong2 *>(sx + k);
+                const ulonglong2 Y = *reinterpret_cast<const ulonglong2 *>(sy + k);
+                const ulonglong2 Z = *reinterpret_cast<const ulonglong2 *>(sz + k);
 #pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const f2 dx = sub2(xi[q], xy.x);
-                    const f2 dy = sub2(yi[q], xy.y);
-                    const f2 dz = sub2(zi[q], zz);
-                    f2 r2 = fma2(dx, dx, EPS2);
-                    r2 = fma2(dy, dy, r2);
-                    r2 = fma2(dz, dz, r2);
-                    float ra, rb;
-                    unpack2(r2, ra, rb);
-                    f2 inv = pack2(rsqrt_mufu(ra), rsqrt_mufu(rb));
-                    if (NEWTON) {  // y <- y (3/2 - r2 y^2 / 2)
-                        const f2 nh = mul2(r2, pack2(-0.5f, -0.5f));
-                        const f2 t = fma2(nh, mul2(inv, inv), pack2(1.5f, 1.5f));
-                        inv = mul2(inv, t);
+                for (int h = 0; h < 2; ++h) {
+                    const f2 xj = h ? X.y : X.x, yj = h ? Y.y : Y.x, zj = h ? Z.y : Z.x;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const f2 dx = sub2(xi[r], xj);
+                        const f2 dy = sub2(yi[r], yj);
+                        const f2 dz = sub2(zi[r], zj);
+                        f2 r2 = fma2(dx, dx, EPS2);
+                        r2 = fma2(dy, dy, r2);
+                        r2 = fma2(dz, dz, r2);
+                        float ra, rb;
+                        unpack2(r2, ra, rb);
+                        f2 inv = pack2(rsqrt_mufu(ra), rsqrt_mufu(rb));
+                        if (NEWTON) {  // y <- y (3/2 - r2 y^2 / 2)
+                            const f2 nh = mul2(r2, pack2(-0.5f, -0.5f));
+                            const f2 t = fma2(nh, mul2(inv, inv), pack2(1.5f, 1.5f));
+                            inv = mul2(inv, t);
+                        }
+                        const f2 inv3 = mul2(mul2(inv, inv), inv);
+                        ax[r] = fma2(dx, inv3, ax[r]);
+                        ay[r] = fma2(dy, inv3, ay[r]);
+                        az[r] = fma2(dz, inv3, az[r]);
                     }
-                    const f2 inv3 = mul2(mul2(inv, inv), inv);
-                    ax[q] = fma2(dx, inv3, ax[q]);
-                    ay[q] = fma2(dy, inv3, ay[q]);
-                    az[q] = fma2(dz, inv3, az[q]);
                 }
             }
         }
         if (KAHAN) {  // fold this tile's sums into the compensated totals
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                f2 y = sub2(ax[q], cx[q]), t = add2(sx[q], y);
-                cx[q] = sub2(sub2(t, sx[q]), y); sx[q] = t; ax[q] = ZERO;
-                y = sub2(ay[q], cy[q]); t = add2(sy[q], y);
-                cy[q] = sub2(sub2(t, sy[q]), y); sy[q] = t; ay[q] = ZERO;
-                y = sub2(az[q], cz[q]); t = add2(sz[q], y);
-                cz[q] = sub2(sub2(t, sz[q]), y); sz[q] = t; az[q] = ZERO;
+            for (int r = 0; r < R; ++r) {
+                const f2 acc[3] = {ax[r], ay[r], az[r]};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const f2 s0 = kreg[r * 6 + 2 * c], c0 = kreg[r * 6 + 2 * c + 1];
+                    const f2 y = sub2(acc[c], c0), t = add2(s0, y);
+                    kreg[r * 6 + 2 * c + 1] = sub2(sub2(t, s0), y);
+                    kreg[r * 6 + 2 * c] = t;
+                }
+                ax[r] = ay[r] = az[r] = ZERO;
             }
         }
     }
 
-    // Combine the L lanes of each i-group and write the chunk's FP64 partial.
+    // Combine the even/odd halves and the L lanes of each i-group; write the FP64 partial.
     double *P = d.partial + (long long)jc * 3 * d.part_stride;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        double v[2][3];
-        float lo, hi, clo, chi;
-        if (KAHAN) {
-            unpack2(sx[q], lo, hi); unpack2(cx[q], clo, chi);
-            v[0][0] = (double)lo - (double)clo; v[1][0] = (double)hi - (double)chi;
-            unpack2(sy[q], lo, hi); unpack2(cy[q], clo, chi);
-            v[0][1] = (double)lo - (double)clo; v[1][1] = (double)hi - (double)chi;
-            unpack2(sz[q], lo, hi); unpack2(cz[q], clo, chi);
-            v[0][2] = (double)lo - (double)clo; v[1][2] = (double)hi - (double)chi;
-        } else {
-            unpack2(ax[q], lo, hi); v[0][0] = lo; v[1][0] = hi;
-            unpack2(ay[q], lo, hi); v[0][1] = lo; v[1][1] = hi;
-            unpack2(az[q], lo, hi); v[0][2] = lo; v[1][2] = hi;
+    for (int r = 0; r < R; ++r) {
+        double v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float lo, hi;
+            if (KAHAN) {
+                float clo, chi;
+                unpack2(kreg[r * 6 + 2 * c], lo, hi);
+                unpack2(kreg[r * 6 + 2 * c + 1], clo, chi);
+                v[c] = ((double)lo - (double)clo) + ((double)hi - (double)chi);
+            } else {
+                unpack2(c == 0 ? ax[r] : (c == 1 ? ay[r] : az[r]), lo, hi);
+                v[c] = (double)lo + (double)hi;
+            }
+#pragma unroll
+            for (int o = 1; o < L; o <<= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
         }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-#pragma unroll
-                for (int o = 1; o < L; o <<= 1) v[h][c] += __shfl_xor_sync(0xffffffffu, v[h][c], o);
-            }
-            const int il = il0 + (2 * q + h) * STRIDE;
-            if (ph == 0 && il < n_e) {
-                const long long p = e_start + il;
-                P[p] = v[h][0];
-                P[d.part_stride + p] = v[h][1];
-                P[2 * d.part_stride + p] = v[h][2];
-            }
+        const int il = il0 + r * STRIDE;
+        if (ph == 0 && il < n_e) {
+            const long long p = e_start + il;
+            P[p] = v[0];
+            P[d.part_stride + p] = v[1];
+            P[2 * d.part_stride + p] = v[2];
         }
     }
 }
@@ -180,8 +190,7 @@ __device__ __forceinline__ int event_of_item(const int *__restrict__ base, int n
 
 template <int R, bool KAHAN, bool NEWTON>
 __global__ void __launch_bounds__(kPairThreads) pair_fp32_kernel(Dev d) {
-    __shared__ ulonglong2 s_xy[kTileJ];
-    __shared__ f2 s_z[kTileJ];
+    __shared__ __align__(16) float s_x[kTileJ], s_y[kTileJ], s_z[kTileJ];
     __shared__ int s_item;
     Ctrl *c = d.ctrl;
     if (step_skipped(c)) return;
@@ -196,9 +205,9 @@ __global__ void __launch_bounds__(kPairThreads) pair_fp32_kernel(Dev d) {
         const int e_start = off[e], n_e = off[e + 1] - e_start;
         const int local = item - d.item_base[e];
         if (lanes_for(n_e, d.shape.small_n) == 1)
-            pair_item_fp32<R, KAHAN, NEWTON, 1>(d, e_start, n_e, local, s_xy, s_z);
+            pair_item_fp32_j<R, KAHAN, NEWTON, 1>(d, e_start, n_e, local, s_x, s_y, s_z);
         else
-            pair_item_fp32<R, KAHAN, NEWTON, 4>(d, e_start, n_e, local, s_xy, s_z);
+            pair_item_fp32_j<R, KAHAN, NEWTON, 4>(d, e_start, n_e, local, s_x, s_y, s_z);
         __syncthreads();  // s_item and the tiles are reused by the next item
     }
 }
