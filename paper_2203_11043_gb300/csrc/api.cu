@@ -48,7 +48,8 @@ bool is_finite(double v) { return std::isfinite(v); }
 
 gc_status validate(const gc_params *p) {
     if (!p || p->abi_version != GC_ABI_VERSION) return GC_ERR_PARAM;
-    if (p->precision < GC_FP64 || p->precision > GC_FP32_KAHAN) return GC_ERR_PARAM;
+    if (p->precision < GC_FP64 || p->precision > GC_FP16X2) return GC_ERR_PARAM;
+    if (p->precision == GC_FP16X2 && p->newton) return GC_ERR_PARAM;
     const double v[] = {p->thickness_um, p->z_well_um, p->a1_V_cm_um, p->a2_V_cm, p->T_K,
                         p->eps_si_rel, p->softening_um, p->dt_s, p->pixel_um};
     for (double x : v)
@@ -509,6 +510,9 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     if (s->phys.coulomb) {
         GC_ALLOC(d.partial, (size_t)cap * 3 * N * 8)
     }
+    if (s->p.precision == GC_FP16X2) {
+        GC_ALLOC(d.ev_ext[0], E * 4) GC_ALLOC(d.ev_ext[1], E * 4)
+    }
     GC_ALLOC(d.keepmask, nchunk * (kChunk / 32) * 4) GC_ALLOC(d.chunk_cnt, nchunk * 4)
     GC_ALLOC(d.ev_off[0], (E + 1) * 4) GC_ALLOC(d.ev_off[1], (E + 1) * 4)
     GC_ALLOC(d.ev_collected_now, E * 4) GC_ALLOC(d.item_base, (E + 1) * 4)
@@ -540,6 +544,10 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, st));
     GC_CUDA(cudaMemsetAsync(d.image, 0, img * 4, st));
     GC_CUDA(cudaMemsetAsync(d.off_image, 0, E * 8, st));
+    if (d.ev_ext[0]) {
+        GC_CUDA(cudaMemsetAsync(d.ev_ext[0], 0, E * 4, st));
+        GC_CUDA(cudaMemsetAsync(d.ev_ext[1], 0, E * 4, st));
+    }
     std::memset(s->h_ctrl, 0, sizeof(Ctrl));
     s->h_ctrl->step_limit = LLONG_MAX;  // open for the step-0 pass
     s->h_ctrl->n_active = (int)n;
@@ -738,7 +746,7 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
     if (n < 0 || n > (1LL << 30)) return GC_ERR_PARAM;
     if (!(softening_um > 0) || !is_finite(softening_um) || !(eps_si_rel > 0) || !is_finite(eps_si_rel))
         return GC_ERR_PARAM;
-    if (precision < GC_FP64 || precision > GC_FP32_KAHAN) return GC_ERR_PARAM;
+    if (precision < GC_FP64 || precision > GC_FP16X2) return GC_ERR_PARAM;
     if (n > 0 && (!xyz_dev || !E_dev)) return GC_ERR_PARAM;
     int cnt = 0;
     cudaError_t e = cudaGetDeviceCount(&cnt);
@@ -777,7 +785,8 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
         if ((e = m.alloc(f64 ? (void **)&d.sh64 : (void **)&d.sh32, (size_t)n * (f64 ? 32 : 16))) ||
             (e = m.alloc((void **)&d.partial, (size_t)S * 3 * n * 8)) ||
             (e = m.alloc((void **)&d.ev_off[0], 8)) || (e = m.alloc((void **)&d.item_base, 8)) ||
-            (e = m.alloc((void **)&d.ev_origin, 24)) || (e = m.alloc((void **)&d.ctrl, sizeof(Ctrl)))) {
+            (e = m.alloc((void **)&d.ev_origin, 24)) || (e = m.alloc((void **)&d.ctrl, sizeof(Ctrl))) ||
+            (precision == GC_FP16X2 && (e = m.alloc((void **)&d.ev_ext[0], 4)))) {
             status = cuda_fail(e);
             break;
         }
@@ -792,6 +801,7 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
         if ((e = cudaMemcpyAsync(d.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemcpyAsync(d.ev_off[0], off, 8, cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemcpyAsync(d.ev_origin, xyz_dev, 24, cudaMemcpyDeviceToDevice, st)) ||
+            (d.ev_ext[0] && (e = cudaMemsetAsync(d.ev_ext[0], 0, 4, st))) ||
             (e = launch_field_prepare(d, xyz_dev, (int)n, f64, st)) || (e = launch_build_items(d, st)) ||
             (e = launch_pair(d, precision, 0, st)) || (e = launch_field_finish(d, (int)n, E_dev, st)) ||
             (e = cudaStreamSynchronize(st))) {

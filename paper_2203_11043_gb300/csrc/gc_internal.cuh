@@ -80,6 +80,7 @@ struct Dev {
     int *item_base;
     unsigned long long *ev_seed;
     double *ev_origin;       // [E][3]
+    unsigned *ev_ext[2];     // FP16x2 form: [E] max |shadow coordinate| (float bits), per buffer
     double *img_origin;      // [E][2]
     int *ev_user;            // internal -> caller event index
     unsigned *image;         // [E_user][H][W]
@@ -156,6 +157,32 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+// ---- packed FP16 helpers (FP16x2 form) -------------------------------------
+// Two FP32 values rounded to one f16x2 register (lo in the low half).
+__device__ __forceinline__ unsigned f2_to_h2(f2 v) {
+    float lo, hi;
+    unpack2(v, lo, hi);
+    unsigned h;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(hi), "f"(lo));
+    return h;
+}
+__device__ __forceinline__ unsigned hfma2(unsigned a, unsigned b, unsigned c) {
+    unsigned d;
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ void h2_to_f(unsigned h, float &lo, float &hi) {
+    asm("{\n\t.reg .b16 l, u;\n\tmov.b32 {l, u}, %2;\n\tcvt.f32.f16 %0, l;\n\t"
+        "cvt.f32.f16 %1, u;\n\t}" : "=f"(lo), "=f"(hi) : "r"(h));
+}
+// Power-of-two scale s for an event whose shadow coordinates satisfy
+// |c| <= ext: then |r_i - r_j|^2 s^2 <= 12 ext^2 s^2 <= 2^15, inside f16 range.
+__device__ __forceinline__ float h2_scale(float ext) {
+    const float e = fmaxf(ext, 1e-6f);
+    const int k = (int)floorf(log2f(52.0f / e));
+    return exp2f((float)min(max(k, -30), 20));
+}
+
 // Hardware reciprocal square root on the MUFU pipe (approximate).
 __device__ __forceinline__ float rsqrt_mufu(float x) {
     float r;

@@ -35,10 +35,15 @@ namespace gc {
 // {x_j, x_j+1}.  Each packed accumulator holds the even-j and odd-j sums of
 // one i; the Kahan state of the cross-tile sums stays in registers.  L lanes
 // share an i-group and split the j range.
-template <int R, bool KAHAN, bool NEWTON, int L>
+//
+// H16 (the FP16x2 form): coordinates are multiplied by the event's
+// power-of-two scale s (exact), the differences are rounded to f16x2 and
+// r^2 s^2 is formed with packed half FMAs; the reciprocal square root and the
+// accumulation stay FP32 and the sum is multiplied by s^2 at the end.
+template <int R, bool KAHAN, bool NEWTON, int L, bool H16>
 __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int n_e, int local,
-                                                 float *__restrict__ sx, float *__restrict__ sy,
-                                                 float *__restrict__ sz) {
+                                                 float scale, float *__restrict__ sx,
+                                                 float *__restrict__ sy, float *__restrict__ sz) {
     constexpr int G = 32 / L;
     constexpr int STRIDE = kPairThreads / L;
     constexpr int IB = R * STRIDE;
@@ -61,6 +66,11 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
         float4 a = make_float4(kSentinel, kSentinel, kSentinel, 0.f);
         const int ia = il0 + r * STRIDE;
         if (ia < n_e) a = d.sh32[e_start + ia];
+        if (H16) {
+            a.x *= scale;
+            a.y *= scale;
+            a.z *= scale;
+        }
         xi[r] = pack2(a.x, a.x);
         yi[r] = pack2(a.y, a.y);
         zi[r] = pack2(a.z, a.z);
@@ -70,8 +80,9 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
             for (int c = 0; c < 6; ++c) kreg[r * 6 + c] = ZERO;
         }
     }
-    const float eps2f = (float)d.phys.eps2;
+    const float eps2f = (float)d.phys.eps2 * (H16 ? scale * scale : 1.0f);
     const f2 EPS2 = pack2(eps2f, eps2f);
+    const unsigned EPS2H = f2_to_h2(EPS2);
 
     const int j0 = jc * jchunk;
     const int j1 = min(n_e, j0 + jchunk);
@@ -89,9 +100,10 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int k = u * kPairThreads + tid;
-            sx[k] = pre[u].x;
-            sy[k] = pre[u].y;
-            sz[k] = pre[u].z;
+            const float sc = H16 ? scale : 1.0f;  // exact (power of two)
+            sx[k] = pre[u].x * sc;
+            sy[k] = pre[u].y * sc;
+            sz[k] = pre[u].z * sc;
         }
         __syncthreads();
         const int cnt = min(TJ, j1 - jt);
@@ -112,11 +124,21 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
                         const f2 dx = sub2(xi[r], xj);
                         const f2 dy = sub2(yi[r], yj);
                         const f2 dz = sub2(zi[r], zj);
-                        f2 r2 = fma2(dx, dx, EPS2);
-                        r2 = fma2(dy, dy, r2);
-                        r2 = fma2(dz, dz, r2);
                         float ra, rb;
-                        unpack2(r2, ra, rb);
+                        f2 r2;
+                        if (H16) {
+                            const unsigned hx = f2_to_h2(dx), hy = f2_to_h2(dy), hz = f2_to_h2(dz);
+                            unsigned h = hfma2(hx, hx, EPS2H);
+                            h = hfma2(hy, hy, h);
+                            h = hfma2(hz, hz, h);
+                            h2_to_f(h, ra, rb);
+                            r2 = pack2(ra, rb);
+                        } else {
+                            r2 = fma2(dx, dx, EPS2);
+                            r2 = fma2(dy, dy, r2);
+                            r2 = fma2(dz, dz, r2);
+                            unpack2(r2, ra, rb);
+                        }
                         f2 inv = pack2(rsqrt_mufu(ra), rsqrt_mufu(rb));
                         if (NEWTON) {  // y <- y (3/2 - r2 y^2 / 2)
                             const f2 nh = mul2(r2, pack2(-0.5f, -0.5f));
@@ -160,6 +182,7 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
                 unpack2(kreg[r * 6 + 2 * c], lo, hi);
                 unpack2(kreg[r * 6 + 2 * c + 1], clo, chi);
                 v[c] = ((double)lo - (double)clo) + ((double)hi - (double)chi);
+                if (H16) v[c] *= (double)scale * (double)scale;
             } else {
                 unpack2(c == 0 ? ax[r] : (c == 1 ? ay[r] : az[r]), lo, hi);
                 v[c] = (double)lo + (double)hi;
@@ -188,13 +211,14 @@ __device__ __forceinline__ int event_of_item(const int *__restrict__ base, int n
     return lo;
 }
 
-template <int R, bool KAHAN, bool NEWTON>
+template <int R, bool KAHAN, bool NEWTON, bool H16>
 __global__ void __launch_bounds__(kPairThreads) pair_fp32_kernel(Dev d) {
     __shared__ __align__(16) float s_x[kTileJ], s_y[kTileJ], s_z[kTileJ];
     __shared__ int s_item;
     Ctrl *c = d.ctrl;
     if (step_skipped(c)) return;
     const int *off = d.ev_off[c->cur];
+    const unsigned *ext = H16 ? d.ev_ext[c->cur] : nullptr;
     const int items = c->items_total;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(&c->work_counter, 1u);
@@ -204,10 +228,11 @@ __global__ void __launch_bounds__(kPairThreads) pair_fp32_kernel(Dev d) {
         const int e = event_of_item(d.item_base, d.n_events, item);
         const int e_start = off[e], n_e = off[e + 1] - e_start;
         const int local = item - d.item_base[e];
+        const float scale = H16 ? h2_scale(__uint_as_float(ext[e])) : 1.0f;
         if (lanes_for(n_e, d.shape.small_n) == 1)
-            pair_item_fp32_j<R, KAHAN, NEWTON, 1>(d, e_start, n_e, local, s_x, s_y, s_z);
+            pair_item_fp32_j<R, KAHAN, NEWTON, 1, H16>(d, e_start, n_e, local, scale, s_x, s_y, s_z);
         else
-            pair_item_fp32_j<R, KAHAN, NEWTON, 4>(d, e_start, n_e, local, s_x, s_y, s_z);
+            pair_item_fp32_j<R, KAHAN, NEWTON, 4, H16>(d, e_start, n_e, local, scale, s_x, s_y, s_z);
         __syncthreads();  // s_item and the tiles are reused by the next item
     }
 }
@@ -273,11 +298,14 @@ __global__ void __launch_bounds__(kPairThreads) pair_fp64_kernel(Dev d) {
 // Host-side launch table.
 typedef void (*PairKernel)(Dev);
 
-static PairKernel fp32_kernel(int R, bool kahan, bool newton) {
-#define GC_PICK(RR)                                                                   \
-    if (R == RR) {                                                                    \
-        if (kahan) return newton ? pair_fp32_kernel<RR, true, true> : pair_fp32_kernel<RR, true, false>; \
-        return newton ? pair_fp32_kernel<RR, false, true> : pair_fp32_kernel<RR, false, false>;         \
+static PairKernel fp32_kernel(int R, bool kahan, bool newton, bool h16) {
+#define GC_PICK(RR)                                                                        \
+    if (R == RR) {                                                                         \
+        if (h16) return pair_fp32_kernel<RR, true, false, true>; /* no Newton step */      \
+        if (kahan) return newton ? pair_fp32_kernel<RR, true, true, false>                 \
+                                 : pair_fp32_kernel<RR, true, false, false>;               \
+        return newton ? pair_fp32_kernel<RR, false, true, false>                           \
+                      : pair_fp32_kernel<RR, false, false, false>;                         \
     }
     GC_PICK(2)
     GC_PICK(4)
@@ -288,8 +316,8 @@ static PairKernel fp32_kernel(int R, bool kahan, bool newton) {
 
 const void *pair_kernel_ptr(int precision, int R, int newton) {
     if (precision == 0) return (const void *)pair_fp64_kernel;
-    if (precision == 1 || precision == 2)
-        return (const void *)fp32_kernel(R, precision == 2, newton != 0);
+    if (precision >= 1 && precision <= 3)
+        return (const void *)fp32_kernel(R, precision >= 2, newton != 0, precision == 3);
     return nullptr;
 }
 

@@ -149,6 +149,10 @@ __global__ void __launch_bounds__(kChunkThreads) integrate_kernel(Dev d) {
     const int n_act = c->n_active;
     const long long step = INIT ? 0 : c->step + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (d.ev_ext[0]) {  // FP16x2 form: the compaction below measures the new extents
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.n_events; e += gridDim.x * blockDim.x)
+            d.ev_ext[cur ^ 1][e] = 0u;
+    }
     const int nchunks = ceil_div(n_act, kChunk);
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         int kept = 0;
@@ -225,18 +229,37 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
             const int p = ch * kChunk + k * kChunkThreads + threadIdx.x;
             const int m = k * (kChunkThreads / 32) + warp;
             const unsigned w = d.keepmask[(long long)ch * WORDS + m];
-            if ((w >> lane) & 1u) {
+            const bool keep = (w >> lane) & 1u;
+            int e = -1;
+            unsigned ext_bits = 0u;
+            if (keep) {
                 const int q = base + s_wpre[m] + __popc(w & ((1u << lane) - 1u));
                 const int id = src[p];
                 dst[q] = id;
-                const int e = d.ev_of_id[id];
+                e = d.ev_of_id[id];
                 const double ox = d.ev_origin[3 * e], oy = d.ev_origin[3 * e + 1],
                              oz = d.ev_origin[3 * e + 2];
-                if (F64)
+                if (F64) {
                     d.sh64[q] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
-                else
-                    d.sh32[q] = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
-                                            (float)(d.pz[id] - oz), 1.0f);
+                } else {
+                    const float4 v = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
+                                                 (float)(d.pz[id] - oz), 1.0f);
+                    d.sh32[q] = v;
+                    ext_bits = __float_as_uint(fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
+                }
+            }
+            if (!F64 && d.ev_ext[0]) {  // FP16x2 form: per-event max |coordinate|
+                unsigned *ext = d.ev_ext[cur ^ 1];
+                const unsigned lead = __ffs(__ballot_sync(0xffffffffu, keep));
+                if (lead) {
+                    const int e0 = __shfl_sync(0xffffffffu, e, lead - 1);
+                    if (__all_sync(0xffffffffu, !keep || e == e0)) {
+                        const unsigned mx = __reduce_max_sync(0xffffffffu, ext_bits);
+                        if (lane == 0) atomicMax(&ext[e0], mx);
+                    } else if (keep) {
+                        atomicMax(&ext[e], ext_bits);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -356,10 +379,24 @@ __global__ void __launch_bounds__(kChunkThreads) build_items_kernel(Dev d) {
 // ---- standalone Eq. 6 helpers -------------------------------------------------------------------
 __global__ void field_prepare_kernel(Dev d, const double *__restrict__ xyz, int n, bool f64) {
     const double ox = d.ev_origin[0], oy = d.ev_origin[1], oz = d.ev_origin[2];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double x = xyz[3LL * i] - ox, y = xyz[3LL * i + 1] - oy, z = xyz[3LL * i + 2] - oz;
-        if (f64) d.sh64[i] = make_double4_32a(x, y, z, 0.0);
-        else d.sh32[i] = make_float4((float)x, (float)y, (float)z, 1.0f);
+    const int stride = gridDim.x * blockDim.x;
+    const int n_round = (n + 31) / 32 * 32;  // whole warps stay in the loop (warp reduction)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        unsigned ext_bits = 0u;
+        if (i < n) {
+            const double x = xyz[3LL * i] - ox, y = xyz[3LL * i + 1] - oy, z = xyz[3LL * i + 2] - oz;
+            if (f64) {
+                d.sh64[i] = make_double4_32a(x, y, z, 0.0);
+            } else {
+                const float4 v = make_float4((float)x, (float)y, (float)z, 1.0f);
+                d.sh32[i] = v;
+                ext_bits = __float_as_uint(fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
+            }
+        }
+        if (d.ev_ext[0]) {  // FP16x2 form: one event, buffer 0
+            const unsigned mx = __reduce_max_sync(0xffffffffu, ext_bits);
+            if ((threadIdx.x & 31) == 0) atomicMax(&d.ev_ext[0][0], mx);
+        }
     }
 }
 

@@ -75,6 +75,14 @@ def test_invalid_params_rejected_before_any_cuda_call(lib, field, value):
     assert not h.value
 
 
+def test_fp16x2_without_newton_step(lib):
+    """The FP16x2 form has no Newton step (a padding pair would give inf * 0)."""
+    import paper_2203_11043_gb300 as gc
+    p = gc.gc_default_params(precision=gc.GC_FP16X2, newton=1)
+    h = ctypes.c_void_p()
+    assert lib.gc_create(ctypes.byref(p), None, ctypes.byref(h)) == gc.GC_ERR_PARAM
+
+
 def test_status_strings(lib):
     import paper_2203_11043_gb300 as gc
     for st in (gc.GC_OK, gc.GC_INCOMPLETE, gc.GC_ERR_PARAM, gc.GC_ERR_ALLOC, gc.GC_ERR_CUDA,

@@ -9,6 +9,11 @@ Tolerances:
     relative to the event origin) amplified by 1/sqrt(d^2 + eps^2); the sum
     adds (tile length + 16) u of sum_j |term_j| with Kahan across tiles, or
     (n + 16) u without it.
+  * FP16x2 form: r^2 is formed from f16 differences (three roundings of
+    2^-11 each on the squares and sums) so each term carries a relative error
+    up to 1.5 * 6 * 2^-11 in r^-3, plus 1.5 * 2^-25 / (r^2 s^2) where r^2 s^2
+    falls below the f16 normal range (s is the event's power-of-two scale),
+    on top of the FP32 bound.
   * FP32 full runs: collected totals exact; sigma_x, sigma_y of the final
     positions within 0.5 % of the oracle's; image L1 difference <= 1 % of the
     charge (the acceptance bar of the method's reduced-precision forms).
@@ -59,8 +64,11 @@ def field_bound(xyz, targets, precision, eps=0.01):
         if precision == 0:
             out[k] = 1e-12 * K * mag.sum() + 1e-300
             continue
-        acc = (TILE_J + 16) if precision == 2 else (n + 16)
+        acc = (n + 16) if precision == 1 else (TILE_J + 16)
         per = mag * (12 * U32 + 20 * U32 * rho / np.sqrt(s2))
+        if precision == 3:
+            sc = 2.0 ** np.floor(np.log2(52.0 / max(rho, 1e-6)))
+            per = per + mag * 1.5 * (6 * 2.0 ** -11 + 2.0 ** -25 / (s2 * sc * sc))
         out[k] = K * (per.sum() + acc * U32 * mag.sum())
     return out
 
@@ -72,7 +80,7 @@ def cloud(n, seed, sigma=0.5, z=300.0):
 
 # ---- Eq. 6 on its own -------------------------------------------------------------------
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 @pytest.mark.parametrize("n", [1, 2, 7, 300, 2000, 9000])
 def test_field_matches_oracle_within_bound(gc, precision, n):
     xyz = cloud(n, seed=n)
@@ -200,7 +208,7 @@ def test_coulomb_off_diffusion_matches_oracle(gc):
     assert err < 1e-9
 
 
-@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2, 3])
 def test_fp32_xray_statistics(gc, precision):
     """FP32 pair sum on the 5.9 keV cloud: collected totals exact, sigma_x and
     sigma_y within 0.5 %, image L1 difference <= 1 % of the charge."""
