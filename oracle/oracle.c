@@ -235,7 +235,7 @@ int64_t orc_run(const orc_params *p, orc_state *s, int64_t steps) {
             for (int64_t k = 0; k < na; ++k) {
                 int64_t i = active[k];
                 advance_one(p, Vth, s->x[i], s->y[i], s->z[i], &Ec[3 * k], s->seeds[e],
-                            (uint32_t)i, step, &newpos[3 * k]);
+                            (uint32_t)(i - s->ev_off[e]), step, &newpos[3 * k]);
             }
             /* commit, then check z (collection at the well) */
             for (int64_t k = 0; k < na; ++k) {

@@ -76,7 +76,9 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 
 /* The three N(0,1) diffusion normals of carrier `id` at step `step`
  * (counter = (id, lo32(step), hi32(step), 0), key = (lo32(seed), hi32(seed)),
- * textbook Box-Muller on the 32-bit outputs). */
+ * textbook Box-Muller on the 32-bit outputs).  `id` is the carrier's index
+ * within its event and `seed` the event's key, so an event's random vectors
+ * do not depend on the other events simulated with it. */
 void orc_diffusion_normals(uint64_t seed, uint32_t id, uint64_t step, double n[3]);
 
 /* Eq. 6 field, in V/cm, at each of the m target carriers targets[t] from
@@ -96,10 +98,12 @@ int orc_init(const orc_params *p, orc_state *s);
  * or -1 on invalid arguments. */
 int64_t orc_run(const orc_params *p, orc_state *s, int64_t steps);
 
-/* One step for a sample of carriers of a single event, without committing:
- * the field at each target comes from all sources src[0..n_src) (active
- * carriers of the event, ascending id); out[t*3+c] is the new position of
- * carrier targets[t] at step `step` (reflection applied, no collection). */
+/* One step for a sample of carriers of a single event whose carriers are
+ * x, y, z[0..) (so an index is also the index within the event), without
+ * committing: the field at each target comes from all sources src[0..n_src)
+ * (active carriers of the event, ascending index); out[t*3+c] is the new
+ * position of carrier targets[t] at step `step` (reflection applied, no
+ * collection). */
 void orc_step_targets(const orc_params *p, const double *x, const double *y,
                       const double *z, const int64_t *src, int64_t n_src,
                       const int64_t *targets, int64_t m, uint64_t seed,

@@ -311,3 +311,22 @@ def test_counts_conserved_batched():
         for e in range(3):
             assert int(sim.image[e].sum()) + int(sim.off_image[e]) + int(act[e]) == sizes[e]
     assert sim.n_active().sum() == 0
+
+
+def test_event_independent_of_batch():
+    """Events are independent (Sec. 5.1: one interaction produces one cloud):
+    an event simulated alone and behind other events of a batch gives
+    identical results, because its random vectors are keyed by its own seed
+    and the carrier's index within the event."""
+    rng = np.random.default_rng(13)
+    a = rng.normal(size=(40, 3)) * 0.4 + np.array([0, 0, 6.0])
+    b = rng.normal(size=(25, 3)) * 0.4 + np.array([0, 0, 3.0])
+    p = O.make_params(img_w=8, img_h=8, pixel_um=2.0)
+    alone = O.Simulation(p, a, seeds=[5], img_origin=[[-8.0, -8.0]])
+    alone.run()
+    both = O.Simulation(p, np.concatenate([b, a]), ev_off=[0, 25, 65], seeds=[9, 5],
+                        img_origin=[[-8.0, -8.0]] * 2)
+    both.run()
+    assert np.array_equal(alone.positions(), both.positions()[25:])
+    assert np.array_equal(alone.collect_step, both.collect_step[25:])
+    assert np.array_equal(alone.image[0], both.image[1])
