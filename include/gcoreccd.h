@@ -117,7 +117,9 @@ gc_status gc_create(const gc_params *p, void *cuda_stream, gc_sim **out);
  * independent events: event e owns rows [event_offsets[e], event_offsets[e+1])
  * (host int64 [n_events+1], starting at 0, non-decreasing, ending at n; NULL
  * means one event).  seeds (host uint64 [n_events]; NULL = all 1) keys each
- * event's Philox diffusion stream.  img_origin_xy (host [n_events][2]; NULL =
+ * event's Philox diffusion stream, whose counter is (index of the carrier
+ * within its event, step), so an event's result does not depend on the other
+ * events loaded with it.  img_origin_xy (host [n_events][2]; NULL =
  * each event's initial x-y centroid minus half the image) is the lower-left
  * image corner.  Carriers are reflected at the back surface if needed and
  * those already in the well are collected at step 0 (Fig. 2 z check).

@@ -467,7 +467,8 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         }
     }
     ioff[E] = pos;
-    std::vector<int> ev_user(order.begin(), order.end());
+    std::vector<int> ev_user(order.begin(), order.end()), ev_first(E);
+    for (int64_t ie = 0; ie < E; ++ie) ev_first[ie] = (int)uoff[order[ie]];
     std::vector<double> hx(std::max<int64_t>(n, 1)), hy(hx.size()), hz(hx.size());
     for (int64_t i = 0; i < n; ++i) {
         hx[i] = xyz[3 * i];
@@ -517,7 +518,8 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     GC_ALLOC(d.ev_off[0], (E + 1) * 4) GC_ALLOC(d.ev_off[1], (E + 1) * 4)
     GC_ALLOC(d.ev_collected_now, E * 4) GC_ALLOC(d.item_base, (E + 1) * 4)
     GC_ALLOC(d.ev_seed, E * 8) GC_ALLOC(d.ev_origin, E * 24) GC_ALLOC(d.img_origin, E * 16)
-    GC_ALLOC(d.ev_user, E * 4) GC_ALLOC(d.image, img * 4) GC_ALLOC(d.off_image, E * 8)
+    GC_ALLOC(d.ev_user, E * 4) GC_ALLOC(d.ev_first, E * 4) GC_ALLOC(d.image, img * 4)
+    GC_ALLOC(d.off_image, E * 8)
     GC_ALLOC(d.ctrl, sizeof(Ctrl))
 #undef GC_ALLOC
     d.part_stride = (long long)N;
@@ -540,6 +542,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     GC_CUDA(cudaMemcpyAsync(d.ev_origin, eorig.data(), E * 24, cudaMemcpyHostToDevice, st));
     GC_CUDA(cudaMemcpyAsync(d.img_origin, iorig.data(), E * 16, cudaMemcpyHostToDevice, st));
     GC_CUDA(cudaMemcpyAsync(d.ev_user, ev_user.data(), E * 4, cudaMemcpyHostToDevice, st));
+    GC_CUDA(cudaMemcpyAsync(d.ev_first, ev_first.data(), E * 4, cudaMemcpyHostToDevice, st));
     GC_CUDA(cudaMemsetAsync(d.collect_step, 0xFF, N * 4, st));
     GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, st));
     GC_CUDA(cudaMemsetAsync(d.image, 0, img * 4, st));

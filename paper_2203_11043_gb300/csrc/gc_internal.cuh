@@ -83,6 +83,7 @@ struct Dev {
     unsigned *ev_ext[2];     // FP16x2 form: [E] max |shadow coordinate| (float bits), per buffer
     double *img_origin;      // [E][2]
     int *ev_user;            // internal -> caller event index
+    int *ev_first;           // internal event -> id of its first carrier
     unsigned *image;         // [E_user][H][W]
     unsigned long long *off_image;
     Ctrl *ctrl;
@@ -118,8 +119,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-// Counter of the diffusion stream: (carrier id, step lo, step hi, 0), keyed by
-// the event seed.
+// Counter of the diffusion stream: (carrier index within its event, step lo,
+// step hi, 0), keyed by the event seed, so an event's random vectors do not
+// depend on the other events of a batch.
 __device__ __forceinline__ uint4 diffusion_bits(unsigned long long seed, int id, long long step) {
     return philox4x32_10(make_uint4((unsigned)id, (unsigned)step,
                                     (unsigned)((unsigned long long)step >> 32), 0u),

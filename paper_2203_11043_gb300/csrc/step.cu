@@ -92,7 +92,7 @@ __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long 
             if (ph.diffusion) {
                 const double sigma = sqrt(2.0 * (1e8 * mu * ph.Vth) * ph.dt);
                 double n[3];
-                normals64(diffusion_bits(d.ev_seed[e], id, step), n);
+                normals64(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
                 dx += sigma * n[0];
                 dy += sigma * n[1];
                 dz += sigma * n[2];
@@ -106,7 +106,7 @@ __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long 
             if (ph.diffusion) {
                 const float sigma = sqrtf(2.0f * (1e8f * mu * (float)ph.Vth) * (float)ph.dt);
                 float n[3];
-                normals32(diffusion_bits(d.ev_seed[e], id, step), n);
+                normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
                 ddx = fmaf(sigma, n[0], ddx);
                 ddy = fmaf(sigma, n[1], ddy);
                 ddz = fmaf(sigma, n[2], ddz);

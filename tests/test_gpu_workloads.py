@@ -1,0 +1,158 @@
+"""The method's workloads on the GPU: batched X-ray events and the muon track.
+
+  * Batched X-rays (uneven N = 267..4800, depths 0..675 um) in one segmented
+    launch per step: counts exact for every event; selected events against
+    the FP64 oracle (sigma_x, sigma_y within 0.5 %, image L1 <= 1 % of the
+    charge, the tolerance of the reduced-precision forms); an event inside the
+    batch gives bit-identical results to the same event run alone (the
+    pipeline is deterministic and a small event is one j-chunk either way).
+  * Muon track: FP32 + Kahan and FP16x2 against the FP64 form on the GPU --
+    the Eq. 6 field at 200,000 holes, and full runs on a 10,000-hole track of
+    the same geometry (sigma_x, sigma_y within 0.5 %, image L1 <= 1 %).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2203_11043_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_11043_gb300 import build
+    build.build()
+    import paper_2203_11043_gb300 as g
+    g.load()
+    return g
+
+
+def run(gc, wl, precision, **kw):
+    p = gc.gc_default_params(precision=precision, img_w=wl.img_w, img_h=wl.img_h, **kw)
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+        st, steps = sim.run(-1)
+        out = sim.collect()
+        out.update(status=st, steps=steps, image=sim.image(), positions=sim.positions(),
+                   stats=sim.stats())
+    return out
+
+
+def event_slice(wl, e):
+    a, b = int(wl.ev_off[e]), int(wl.ev_off[e + 1])
+    return I.Workload(f"event{e}", wl.xyz[a:b], np.array([0, b - a], np.int64), wl.seeds[e:e + 1],
+                      wl.img_origin[e:e + 1], wl.img_w, wl.img_h)
+
+
+def assert_statistics(pos_a, pos_b, img_a, img_b, n):
+    for c in (0, 1):
+        assert pos_a[:, c].std() == pytest.approx(pos_b[:, c].std(), rel=5e-3)
+    l1 = np.abs(img_a.astype(np.int64) - img_b.astype(np.int64)).sum()
+    assert l1 <= 0.01 * n, (l1, n)
+
+
+@pytest.fixture(scope="module")
+def batch(gc):
+    wl = I.xray_batch(n_events=512)
+    return wl, run(gc, wl, gc.GC_FP32_KAHAN, pair_R=4, jchunk=8192)
+
+
+def test_batch_counts_exact(gc, batch):
+    wl, res = batch
+    assert res["status"] == gc.GC_OK
+    sizes = np.diff(wl.ev_off)
+    assert np.array_equal(res["n_collected"], sizes)
+    assert np.all(res["n_active"] == 0)
+    img_sum = res["image"].reshape(wl.n_events, -1).sum(axis=1).astype(np.int64)
+    assert np.array_equal(img_sum + res["n_offimage"], sizes)
+    assert np.all(res["collect_step"] >= 0)
+    # the device's pair count is sum over steps and events of N_active^2
+    cs = res["collect_step"]
+    total = 0
+    for e in range(wl.n_events):
+        c = np.sort(cs[wl.ev_off[e]:wl.ev_off[e + 1]])
+        c = c[c > 0]
+        # active at the start of step s = carriers collected at a step >= s
+        steps = np.arange(1, c.max() + 1) if len(c) else np.arange(0)
+        act = len(c) - np.searchsorted(c, steps, side="left")
+        total += int((act.astype(np.int64) ** 2).sum())
+    assert res["stats"]["pair_interactions"] == float(total)
+
+
+def test_batch_events_against_oracle(gc, batch):
+    """A few small and shallow events of the batch against the FP64 oracle."""
+    wl, res = batch
+    sizes = np.diff(wl.ev_off)
+    depth = np.array([wl.xyz[wl.ev_off[e]:wl.ev_off[e + 1], 2].mean() for e in range(wl.n_events)])
+    cost = sizes.astype(float) ** 2 * depth
+    pick = [int(e) for e in np.argsort(cost)[:4]] + [int(np.argmax(sizes * (depth < 60)))]
+    for e in pick:
+        ev = event_slice(wl, e)
+        ref = O.Simulation(O.make_params(img_w=wl.img_w, img_h=wl.img_h), ev.xyz, ev.ev_off,
+                           ev.seeds, ev.img_origin)
+        ref.run()
+        a, b = int(wl.ev_off[e]), int(wl.ev_off[e + 1])
+        assert np.all(ref.collect_step >= 0)
+        assert_statistics(res["positions"][a:b], ref.positions(), res["image"][e], ref.image[0], b - a)
+
+
+def test_batched_equals_per_event(gc, batch):
+    """An event inside the batch is bit-identical to the same event alone."""
+    wl, res = batch
+    sizes = np.diff(wl.ev_off)
+    for e in [int(np.argmin(sizes)), 7, int(np.argmax(sizes))]:
+        ev = event_slice(wl, e)
+        alone = run(gc, ev, gc.GC_FP32_KAHAN, pair_R=4, jchunk=8192)
+        a, b = int(wl.ev_off[e]), int(wl.ev_off[e + 1])
+        assert np.array_equal(alone["positions"], res["positions"][a:b])
+        assert np.array_equal(alone["collect_step"], res["collect_step"][a:b])
+        assert np.array_equal(alone["image"][0], res["image"][e])
+
+
+def test_muon_field_forms_against_fp64(gc):
+    """Eq. 6 on the 200,000-hole track: FP32 + Kahan and FP16x2 against the
+    FP64 form on the GPU (relative L2 error of the field)."""
+    import torch
+    wl = I.muon_track()
+    t = torch.tensor(wl.xyz, dtype=torch.float64, device="cuda")
+    out = {}
+    for prec in (gc.GC_FP64, gc.GC_FP32_KAHAN, gc.GC_FP16X2):
+        E = torch.empty_like(t)
+        gc.gc_coulomb_field(t, wl.n, 0.01, 11.7, prec, E, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        out[prec] = E.cpu().numpy()
+    ref = out[gc.GC_FP64]
+    norm = np.linalg.norm(ref)
+    err32 = np.linalg.norm(out[gc.GC_FP32_KAHAN] - ref) / norm
+    err16 = np.linalg.norm(out[gc.GC_FP16X2] - ref) / norm
+    print(f"muon field relative L2 error: FP32+Kahan {err32:.3e}, FP16x2 {err16:.3e}")
+    # The FP32 shadow rounds coordinates up to ~1.25 mm from the event centroid
+    # to 2^-24 relative (~1e-4 um), against nearest-neighbour distances of
+    # 0.01-0.1 um: the closest pairs, which dominate |E|, carry errors of
+    # 1e-3 to 1e-2.  The FP16x2 form adds f16 rounding of r^2 (and f16
+    # subnormals for the closest pairs at this event's scale).
+    assert err32 < 5e-3
+    assert err16 < 2e-1
+
+
+@pytest.fixture(scope="module")
+def muon10k(gc):
+    wl = I.muon_track(n=10_000, seed=2)
+    return wl, run(gc, wl, gc.GC_FP64)
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+def test_muon_run_forms_against_fp64(gc, muon10k, precision):
+    """Full runs of a 10,000-hole track (the 2.5 mm geometry at 1/20 of the
+    density): FP32 + Kahan and FP16x2 against the FP64 form on the GPU."""
+    wl, ref = muon10k
+    got = run(gc, wl, precision)
+    assert got["status"] == ref["status"] == gc.GC_OK
+    assert got["n_collected"][0] == ref["n_collected"][0] == wl.n
+    assert_statistics(got["positions"], ref["positions"], got["image"][0], ref["image"][0], wl.n)
+    d = np.abs(got["positions"] - ref["positions"])[:, :2].max(axis=1)
+    print(f"precision {precision}: per-hole final |dxy| vs FP64: median {np.median(d):.2e} um, "
+          f"99th pct {np.percentile(d, 99):.2e} um, max {d.max():.2e} um")
