@@ -35,9 +35,32 @@ from paper_2203_11043_gb300 import inputs  # noqa: E402
 FP32_OPS_PER_PAIR = 11  # 3 sub + 3 fma (r^2) + 2 mul (r^-3) + 3 fma (accumulate); rsqrt on MUFU
 FP32_LANES_PER_SM = 128
 METRIC = "pair-interactions/s"
-WORKLOAD = ("track-bundle-1M: one event of 1,048,576 holes in 16 straight muon-like tracks "
-            "(65,536 holes each, 2.5 mm long, 0.5 um jitter, 30 um apart) across a 675 um CCD; "
-            "E = 2 z - 1500 V/cm, T = 140 K, dt = 10 ps, eps = 0.01 um, 512 x 512 pixels of 15 um")
+FIELD = "E = 2 z - 1500 V/cm, T = 140 K, dt = 10 ps, eps = 0.01 um"
+WORKLOADS = {
+    "bundle": ("track-bundle-1M: one event of 1,048,576 holes in 16 straight muon-like tracks "
+               "(65,536 holes each, 2.5 mm long, 0.5 um jitter, 30 um apart) across a 675 um CCD; "
+               + FIELD + ", 512 x 512 pixels of 15 um"),
+    "xray-batch": ("xray-batch-4096: 4096 independent X-ray clouds, E ~ U(1, 18) keV, N = E / 3.75 eV "
+                   "(267..4800 holes), sigma 0.3 um, depth ~ U(0, 675) um, seeds 1..4096; " + FIELD
+                   + ", 64 x 64 pixels of 15 um per event"),
+    "muon": ("muon-200k: one straight 2.5 mm track of 200,000 holes across the 675 um CCD, "
+             "0.5 um jitter; " + FIELD + ", 512 x 512 pixels of 15 um"),
+    "xray": ("xray-5.9keV: one cloud of 1573 holes, sigma 0.3 um, depth from seed 1; " + FIELD
+             + ", 64 x 64 pixels of 15 um"),
+}
+WORKLOAD = WORKLOADS["bundle"]
+
+
+def make_workload(name: str):
+    if name == "bundle":
+        return inputs.track_bundle()
+    if name == "xray-batch":
+        return inputs.xray_batch()
+    if name == "muon":
+        return inputs.muon_track()
+    if name == "xray":
+        return inputs.xray_5p9kev()
+    raise ValueError(name)
 
 
 def dist_env():
@@ -168,6 +191,62 @@ def reference_arm(args):
     return 0
 
 
+def to_completion(args):
+    """One run of the workload until every hole is collected (CUDA graphs),
+    timed with CUDA events; optionally the first M events run one simulation
+    each, for the batched-vs-per-event comparison."""
+    import torch
+    import paper_2203_11043_gb300 as gc
+    from paper_2203_11043_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    wl = make_workload(args.workload)
+    prec = gc.GC_FP32_KAHAN
+
+    def timed_run(w):
+        p = gc.gc_default_params(precision=prec, img_w=w.img_w, img_h=w.img_h, pair_R=args.pair_R,
+                                 coulomb=args.coulomb)
+        with gc.Simulation(p, w.xyz, w.ev_off, w.seeds, w.img_origin, stream=stream.cuda_stream) as s:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            st, steps = s.run(-1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            stats = s.stats()
+        return a.elapsed_time(b) / 1e3, steps, stats
+
+    secs, steps, stats = timed_run(wl)
+    line = {"metric": METRIC, "value": stats["pair_interactions"] / secs, "unit": "pairs/s",
+            "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": 1e3 * secs / max(steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "mode": "to completion", "coulomb": args.coulomb,
+            "config": {"workload": WORKLOADS[args.workload], "n_carriers": wl.n,
+                       "events": wl.n_events, "pair_R": stats["pair_variant"],
+                       "jchunk": stats["jchunk"], "pair_blocks": stats["pair_blocks"]},
+            "carrier_steps_per_s": stats["carrier_steps"] / secs, "seconds": secs,
+            "pair_interactions": stats["pair_interactions"], "carrier_steps": stats["carrier_steps"]}
+    if args.per_event and wl.n_events > 1:
+        m = min(args.per_event, wl.n_events)
+        sub = inputs.Workload(wl.name, wl.xyz[:wl.ev_off[m]], wl.ev_off[:m + 1].copy(), wl.seeds[:m],
+                              wl.img_origin[:m], wl.img_w, wl.img_h)
+        bsecs, _, bst = timed_run(sub)
+        tot, pairs = 0.0, 0.0
+        for e in range(m):
+            a, b = int(wl.ev_off[e]), int(wl.ev_off[e + 1])
+            ev = inputs.Workload(wl.name, wl.xyz[a:b], np.array([0, b - a], np.int64),
+                                 wl.seeds[e:e + 1], wl.img_origin[e:e + 1], wl.img_w, wl.img_h)
+            es, _, est = timed_run(ev)
+            tot += es
+            pairs += est["pair_interactions"]
+        line["per_event_launches"] = {"events": m, "batched_pairs_per_s": bst["pair_interactions"] / bsecs,
+                                      "per_event_pairs_per_s": pairs / tot,
+                                      "batched_over_per_event": (bst["pair_interactions"] / bsecs) / (pairs / tot)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,10 +259,19 @@ def main():
     ap.add_argument("--n-carriers", type=int, default=0,
                     help="run on a random sub-sample of the bundle (profiling small cases)")
     ap.add_argument("--pair-R", type=int, default=0, help="force the pair-kernel register blocking")
+    ap.add_argument("--workload", default="bundle", choices=sorted(WORKLOADS))
+    ap.add_argument("--to-completion", action="store_true",
+                    help="time one run until every hole is collected (graphs, no per-step flush)")
+    ap.add_argument("--coulomb", type=int, default=1, choices=[0, 1],
+                    help="with --to-completion: 0 runs the O(N) Coulomb-off path")
+    ap.add_argument("--per-event", type=int, default=0,
+                    help="with --to-completion: also run the first M events one simulation each")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.to_completion:
+        return to_completion(args)
 
     import torch
     import paper_2203_11043_gb300 as gc
@@ -199,7 +287,7 @@ def main():
     stream = torch.cuda.current_stream()
     sms, ccmaj, ccmin = gc.gc_device_info()
 
-    wl = inputs.track_bundle()
+    wl = make_workload(args.workload)
     if args.n_carriers:
         wl = inputs.subsample(wl, args.n_carriers, seed=3)
     # every rank runs an independent replica of the event (replicas only: the
@@ -263,7 +351,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_carriers": wl.n, "events": 1,
+            "config": {"workload": WORKLOADS[args.workload], "n_carriers": wl.n, "events": wl.n_events,
                        "precision": "FP32 pair sum with Kahan across j-tiles; FP64 positions",
                        "pair_R": after["pair_variant"], "pair_blocks": after["pair_blocks"],
                        "jchunk": after["jchunk"], "l2": "flushed between timed steps (256 MB write)",
