@@ -68,6 +68,28 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def aggregate(time_ms: float, work, device="cpu"):
+    """Whole-job figures over the ranks of an initialised process group: the
+    max of the timed durations and the sum of the work (pairs, carrier-steps).
+    Without a group (or with one rank) the inputs come back unchanged."""
+    import torch
+    import torch.distributed as dist
+    work = [float(w) for w in work]
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(time_ms), work
+    t = torch.tensor([float(time_ms)], dtype=torch.float64, device=device)
+    w = torch.tensor(work, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t[0]), [float(x) for x in w]
+
+
+def replica_seeds(seeds, rank: int):
+    """Each rank simulates an independent replica of the workload: the event
+    seeds are offset by the rank (replicas only; the event is not sharded)."""
+    return np.asarray(seeds, dtype=np.uint64) + np.uint64(rank)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -158,7 +180,9 @@ def reference_arm(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    wl = inputs.track_bundle()
+    wl = make_workload(args.workload)
+    if args.n_carriers:
+        wl = inputs.subsample(wl, args.n_carriers, seed=3)
     per_step = max(2.0, min(4.0, 150.0 / max(1, args.steps + args.warmup)))
     import oracle as O
     p = O.make_params(img_w=wl.img_w, img_h=wl.img_h)
@@ -183,7 +207,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n_carriers": wl.n},
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "n_carriers": wl.n},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"{m} randomly chosen holes per step, field from all {wl.n}"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -292,7 +316,7 @@ def main():
         wl = inputs.subsample(wl, args.n_carriers, seed=3)
     # every rank runs an independent replica of the event (replicas only: the
     # single event is not sharded); seeds differ per rank
-    seeds = wl.seeds + np.uint64(rank)
+    seeds = replica_seeds(wl.seeds, rank)
     params = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
                                   graph_steps=1, timing=1, pair_R=args.pair_R)
     sim = gc.Simulation(params, wl.xyz, wl.ev_off, seeds, wl.img_origin, stream=stream.cuda_stream)
@@ -325,12 +349,7 @@ def main():
     pair_ms = after["pair_kernel_ms"] - base["pair_kernel_ms"]
     pair_launches = after["pair_kernel_launches"] - base["pair_kernel_launches"]
     steps_done = after["steps"] - base["steps"]
-    if world > 1:
-        t = torch.tensor([total_ms, pairs, csteps], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        total_ms, pairs, csteps = float(mx[0]), float(t[1]), float(t[2])
+    total_ms, (pairs, csteps) = aggregate(total_ms, [pairs, csteps], device="cuda")
     value = pairs / (total_ms / 1e3)
     clocks = clk.summary()
 
@@ -396,13 +415,8 @@ def main():
         t1 = time.perf_counter()
         h2d = wl.xyz.nbytes + 8 * wl.n  # FP64 positions, active-id list and event map
         d2h = res["final_xy"].nbytes + res["collect_step"].nbytes + img.nbytes
-        e2e_val = st3["pair_interactions"] / (t1 - t0)
-        if world > 1:
-            t = torch.tensor([t1 - t0, st3["pair_interactions"]], dtype=torch.float64, device="cuda")
-            mx = t.clone()
-            torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-            e2e_val = float(t[1]) / float(mx[0])
+        e2e_s, (e2e_pairs,) = aggregate(t1 - t0, [st3["pair_interactions"]], device="cuda")
+        e2e_val = e2e_pairs / e2e_s
         line["e2e"] = {"value": e2e_val, "unit": "pairs/s",
                        "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
                        "steps": e2e_steps,
