@@ -211,8 +211,11 @@ __device__ __forceinline__ int event_of_item(const int *__restrict__ base, int n
     return lo;
 }
 
+// Min blocks = 1 lets ptxas keep many independent pair chains in registers
+// (R = 4: ~246 registers, 2 blocks per SM); measured faster than letting it
+// trade registers for occupancy.
 template <int R, bool KAHAN, bool NEWTON, bool H16>
-__global__ void __launch_bounds__(kPairThreads) pair_fp32_kernel(Dev d) {
+__global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
     __shared__ __align__(16) float s_x[kTileJ], s_y[kTileJ], s_z[kTileJ];
     __shared__ int s_item;
     Ctrl *c = d.ctrl;
