@@ -34,6 +34,10 @@ from paper_2203_11043_gb300 import inputs  # noqa: E402
 
 FP32_OPS_PER_PAIR = 11  # 3 sub + 3 fma (r^2) + 2 mul (r^-3) + 3 fma (accumulate); rsqrt on MUFU
 FP32_LANES_PER_SM = 128
+# Coulomb-off step (integrate + compaction), algorithmic HBM bytes per
+# carrier-step: integrate reads id 4 + event 4 + FP64 position 24 and writes
+# the position 24 (+ 1 keep bit); compaction reads and writes the id (4 + 4).
+BYTES_PER_CARRIER_STEP_O_N = 64
 METRIC = "pair-interactions/s"
 FIELD = "E = 2 z - 1500 V/cm, T = 140 K, dt = 10 ps, eps = 0.01 um"
 WORKLOADS = {
@@ -88,6 +92,23 @@ def replica_seeds(seeds, rank: int):
     """Each rank simulates an independent replica of the workload: the event
     seeds are offset by the rank (replicas only; the event is not sharded)."""
     return np.asarray(seeds, dtype=np.uint64) + np.uint64(rank)
+
+
+def recorded_traffic():
+    """DRAM bytes per pair-kernel launch from the committed ncu summary of the
+    track-bundle workload, only while the kernel source is the one that was
+    profiled (otherwise None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "pair_fp32_track_bundle_traffic.md")
+    try:
+        text = open(path).read()
+        src = open(os.path.join(ROOT, "paper_2203_11043_gb300", "csrc", "pair.cu"), "rb").read()
+    except OSError:
+        return None
+    fields = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("traffic_", "kernel_")))
+    if fields.get("kernel_source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+        return None
+    return float(fields["traffic_bytes_per_launch"])
 
 
 def measured_peaks():
@@ -287,7 +308,7 @@ def main():
     ap.add_argument("--to-completion", action="store_true",
                     help="time one run until every hole is collected (graphs, no per-step flush)")
     ap.add_argument("--coulomb", type=int, default=1, choices=[0, 1],
-                    help="with --to-completion: 0 runs the O(N) Coulomb-off path")
+                    help="0 runs the O(N) Coulomb-off path (metric: carrier-steps/s)")
     ap.add_argument("--per-event", type=int, default=0,
                     help="with --to-completion: also run the first M events one simulation each")
     args = ap.parse_args()
@@ -318,7 +339,7 @@ def main():
     # single event is not sharded); seeds differ per rank
     seeds = replica_seeds(wl.seeds, rank)
     params = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
-                                  graph_steps=1, timing=1, pair_R=args.pair_R)
+                                  graph_steps=1, timing=1, pair_R=args.pair_R, coulomb=args.coulomb)
     sim = gc.Simulation(params, wl.xyz, wl.ev_off, seeds, wl.img_origin, stream=stream.cuda_stream)
     st0 = sim.stats()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -348,6 +369,8 @@ def main():
     csteps = after["carrier_steps"] - base["carrier_steps"]
     pair_ms = after["pair_kernel_ms"] - base["pair_kernel_ms"]
     pair_launches = after["pair_kernel_launches"] - base["pair_kernel_launches"]
+    step_kernels_ms = (after["integrate_kernel_ms"] - base["integrate_kernel_ms"]
+                       + after["compact_kernel_ms"] - base["compact_kernel_ms"])
     steps_done = after["steps"] - base["steps"]
     total_ms, (pairs, csteps) = aggregate(total_ms, [pairs, csteps], device="cuda")
     value = pairs / (total_ms / 1e3)
@@ -358,8 +381,10 @@ def main():
     peak = sms * FP32_LANES_PER_SM * max_mhz * 1e6 / FP32_OPS_PER_PAIR
     pairs_per_launch = pairs / max(1, pair_launches) / max(1, world)
     achieved = pairs_per_launch / (pair_ms / max(1, pair_launches) / 1e3) if pair_launches else None
+    traffic = recorded_traffic() if (args.workload == "bundle" and not args.n_carriers) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": "pair_fp32_kernel<R,Kahan>",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz "
                               f"(sm_max_mhz of MEASURED_PEAKS.json) / {FP32_OPS_PER_PAIR} FP32 ops per pair",
@@ -379,6 +404,20 @@ def main():
             "roofline": roofline, "gpu_launches": int(steps_done * after["launches_per_step"]),
             "clocks": clocks}
 
+    if not args.coulomb:  # the O(N) path: carrier-steps/s against the HBM copy bandwidth
+        hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+        bw = BYTES_PER_CARRIER_STEP_O_N * csteps / max(world, 1) / (step_kernels_ms / 1e3)
+        line.update(metric="carrier-steps/s", value=csteps / (total_ms / 1e3), unit="carrier-steps/s",
+                    dtype="f64")
+        line["config"]["precision"] = "Coulomb off: FP32 mobility/diffusion, FP64 positions"
+        line["roofline"] = {"bound": "hbm", "achieved": bw / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                            "frac": bw / hbm, "traffic": None,
+                            "kernel": "integrate_kernel + compact_kernel",
+                            "algorithmic_bytes_per_carrier_step": BYTES_PER_CARRIER_STEP_O_N,
+                            "peak_basis": "hbm_gbs of MEASURED_PEAKS.json (STREAM-style copy)",
+                            "step_kernels_share_of_step": step_kernels_ms / max(total_ms, 1e-9)}
+        args.no_fp64 = True
+        args.no_e2e = True
     # FP64 form vs FP32 form on one track of the same workload (like for like)
     if not args.no_fp64 and rank == 0:
         sub = inputs.subsample(wl, 65536, seed=3)
@@ -423,7 +462,7 @@ def main():
                        "includes": "gc_create + gc_load_carriers (host positions) + gc_run + gc_collect + "
                                    "gc_image (host outputs), host wall clock"}
 
-    if not args.no_cpu_baseline and rank == 0 and world == 1:
+    if not args.no_cpu_baseline and rank == 0 and world == 1 and args.coulomb:
         line["cpu_baseline"] = cpu_baseline(wl)
     sim.close()
     if rank == 0:

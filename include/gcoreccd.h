@@ -99,6 +99,9 @@ typedef struct {
     int32_t launches_per_step;/* kernels launched per time step */
     double pair_kernel_ms;    /* with timing on: summed device time of the pair kernel */
     int64_t pair_kernel_launches; /* with timing on: pair-kernel launches that did work */
+    double integrate_kernel_ms;   /* with timing on: summed device time of the integrate kernel */
+    double compact_kernel_ms;     /* with timing on: summed device time of the compaction kernel */
+    int64_t timed_steps;          /* with timing on: steps whose kernels were timed */
 } gc_stats;
 
 /* Defaults: the CCD of the X-ray and muon workloads (thickness 675 um,

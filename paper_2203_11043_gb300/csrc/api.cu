@@ -146,9 +146,10 @@ struct gc_sim {
     int integ_grid = 1;
     int launches_per_step = 0;
     long long part_cap_chunks = 1;   // j-chunks the partial buffer can hold
-    std::vector<cudaEvent_t> ev_a, ev_b;  // timing: around each pair launch of a graph
-    double pair_ms = 0.0;
-    long long pair_launches = 0;
+    // timing: before the pair kernel, after it, after integrate, after compact
+    std::vector<cudaEvent_t> ev_a, ev_b, ev_c, ev_d;
+    double pair_ms = 0.0, integ_ms = 0.0, compact_ms = 0.0;
+    long long pair_launches = 0, timed_steps = 0;
 };
 
 namespace {
@@ -163,12 +164,12 @@ void free_state(gc_sim *s) {
         cudaGraphExecDestroy(s->graph);
         s->graph = nullptr;
     }
-    for (cudaEvent_t e : s->ev_a) cudaEventDestroy(e);
-    for (cudaEvent_t e : s->ev_b) cudaEventDestroy(e);
-    s->ev_a.clear();
-    s->ev_b.clear();
-    s->pair_ms = 0.0;
-    s->pair_launches = 0;
+    for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
+        for (cudaEvent_t e : *v) cudaEventDestroy(e);
+        v->clear();
+    }
+    s->pair_ms = s->integ_ms = s->compact_ms = 0.0;
+    s->pair_launches = s->timed_steps = 0;
     s->mem.release();
     s->loaded = false;
     s->dev = Dev{};
@@ -177,12 +178,14 @@ void free_state(gc_sim *s) {
 // One time step; k indexes the step inside a captured graph (timing events).
 gc_status enqueue_step(gc_sim *s, int k) {
     const bool f64 = fp64_mode(s);
-    const bool timed = s->p.timing && s->phys.coulomb && k < (int)s->ev_a.size();
+    const bool timed = s->p.timing && k < (int)s->ev_a.size();
     if (timed) GC_CUDA(cudaEventRecord(s->ev_a[k], s->stream));
     if (s->phys.coulomb) GC_CUDA(launch_pair(s->dev, s->p.precision, s->p.newton, s->stream));
     if (timed) GC_CUDA(cudaEventRecord(s->ev_b[k], s->stream));
     GC_CUDA(launch_integrate(s->dev, f64, false, s->integ_grid, s->stream));
+    if (timed) GC_CUDA(cudaEventRecord(s->ev_c[k], s->stream));
     GC_CUDA(launch_compact(s->dev, f64, s->integ_grid, s->stream));
+    if (timed) GC_CUDA(cudaEventRecord(s->ev_d[k], s->stream));
     GC_CUDA(launch_finalize(s->dev, false, s->stream));
     return GC_OK;
 }
@@ -577,12 +580,9 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     if (r != GC_OK) return r;
     s->launches_per_step = (s->phys.coulomb ? 1 : 0) + 3;
     if (s->p.timing) {
-        const int ne = 1;
-        s->ev_a.resize(ne);
-        s->ev_b.resize(ne);
-        for (int k = 0; k < ne; ++k) {
-            GC_CUDA(cudaEventCreate(&s->ev_a[k]));
-            GC_CUDA(cudaEventCreate(&s->ev_b[k]));
+        for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
+            v->resize(1);
+            GC_CUDA(cudaEventCreate(&(*v)[0]));
         }
     }
     s->loaded = true;
@@ -620,11 +620,18 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
                 gc_status q = read_ctrl(s);
                 if (q != GC_OK) return q;
                 const long long did = std::min<long long>(K, s->h_ctrl->step - before);
-                for (long long k = 0; k < did && s->phys.coulomb; ++k) {
+                for (long long k = 0; k < did; ++k) {
                     float ms = 0.f;
-                    GC_CUDA(cudaEventElapsedTime(&ms, s->ev_a[k], s->ev_b[k]));
-                    s->pair_ms += ms;
-                    s->pair_launches += 1;
+                    if (s->phys.coulomb) {
+                        GC_CUDA(cudaEventElapsedTime(&ms, s->ev_a[k], s->ev_b[k]));
+                        s->pair_ms += ms;
+                        s->pair_launches += 1;
+                    }
+                    GC_CUDA(cudaEventElapsedTime(&ms, s->ev_b[k], s->ev_c[k]));
+                    s->integ_ms += ms;
+                    GC_CUDA(cudaEventElapsedTime(&ms, s->ev_c[k], s->ev_d[k]));
+                    s->compact_ms += ms;
+                    s->timed_steps += 1;
                 }
             }
             return GC_OK;
@@ -741,6 +748,9 @@ gc_status gc_get_stats(gc_sim *s, gc_stats *out) {
     out->launches_per_step = s->launches_per_step;
     out->pair_kernel_ms = s->pair_ms;
     out->pair_kernel_launches = s->pair_launches;
+    out->integrate_kernel_ms = s->integ_ms;
+    out->compact_kernel_ms = s->compact_ms;
+    out->timed_steps = s->timed_steps;
     return GC_OK;
 }
 

@@ -236,19 +236,21 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
                 const int q = base + s_wpre[m] + __popc(w & ((1u << lane) - 1u));
                 const int id = src[p];
                 dst[q] = id;
-                e = d.ev_of_id[id];
-                const double ox = d.ev_origin[3 * e], oy = d.ev_origin[3 * e + 1],
-                             oz = d.ev_origin[3 * e + 2];
-                if (F64) {
-                    d.sh64[q] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
-                } else {
-                    const float4 v = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
-                                                 (float)(d.pz[id] - oz), 1.0f);
-                    d.sh32[q] = v;
-                    ext_bits = __float_as_uint(fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
+                if (d.phys.coulomb) {  // the O(N) path reads no shadow
+                    e = d.ev_of_id[id];
+                    const double ox = d.ev_origin[3 * e], oy = d.ev_origin[3 * e + 1],
+                                 oz = d.ev_origin[3 * e + 2];
+                    if (F64) {
+                        d.sh64[q] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
+                    } else {
+                        const float4 v = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
+                                                     (float)(d.pz[id] - oz), 1.0f);
+                        d.sh32[q] = v;
+                        ext_bits = __float_as_uint(fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
+                    }
                 }
             }
-            if (!F64 && d.ev_ext[0]) {  // FP16x2 form: per-event max |coordinate|
+            if (!F64 && d.ev_ext[0] && d.phys.coulomb) {  // FP16x2 form: per-event max |coordinate|
                 unsigned *ext = d.ev_ext[cur ^ 1];
                 const unsigned lead = __ffs(__ballot_sync(0xffffffffu, keep));
                 if (lead) {

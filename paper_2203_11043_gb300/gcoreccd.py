@@ -70,6 +70,9 @@ class GcStats(ctypes.Structure):
         ("launches_per_step", ctypes.c_int32),
         ("pair_kernel_ms", ctypes.c_double),
         ("pair_kernel_launches", ctypes.c_int64),
+        ("integrate_kernel_ms", ctypes.c_double),
+        ("compact_kernel_ms", ctypes.c_double),
+        ("timed_steps", ctypes.c_int64),
     ]
 
 

@@ -338,3 +338,24 @@ def test_timing_mode_counts_pair_launches(gc):
         else:
             assert st["pair_kernel_launches"] == 0
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_coulomb_off_lateral_spread_at_scale(gc):
+    """Coulomb off, 10^6 holes from a point at z0 = 300 um: the lateral
+    variance of the collected holes equals 2 int D dt = 2e4 (kT/q) / a1 *
+    ln(a2 / (a2 - a1 z0)) (the mobility cancels), 61.627 um^2, within the
+    statistical error sqrt(2/N) and the O(dt) Euler error."""
+    import math
+    n, z0 = 1_000_000, 300.0
+    xyz = np.tile(np.array([[0.0, 0.0, z0]]), (n, 1))
+    p = gc.gc_default_params(precision=2, coulomb=0, img_w=64, img_h=64)
+    with gc.Simulation(p, xyz, img_origin=[[-480.0, -480.0]]) as sim:
+        st, steps = sim.run(-1)
+        r = sim.collect()
+    assert st == gc.GC_OK and r["n_collected"][0] == n
+    want = 2e4 * (1.380649e-23 * 140.0 / 1.602176634e-19) / 2.0 * math.log(1500.0 / 900.0)
+    tol = 5 * math.sqrt(2 / n) + 3e-3
+    for c in (0, 1):
+        assert r["final_xy"][:, c].var() == pytest.approx(want, rel=tol)
+    # the mean collection step is the drift time t(300 um) = 12.3143 ns (1231.4 steps)
+    assert r["collect_step"].mean() == pytest.approx(1231.4, rel=5e-3)
