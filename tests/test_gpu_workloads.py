@@ -156,3 +156,18 @@ def test_muon_run_forms_against_fp64(gc, muon10k, precision):
     d = np.abs(got["positions"] - ref["positions"])[:, :2].max(axis=1)
     print(f"precision {precision}: per-hole final |dxy| vs FP64: median {np.median(d):.2e} um, "
           f"99th pct {np.percentile(d, 99):.2e} um, max {d.max():.2e} um")
+
+
+def test_carriers_from_file_through_the_abi(gc, tmp_path):
+    """Positions read from a text file (Sec. 3.2) give the oracle's result."""
+    from paper_2203_11043_gb300 import carrier_io
+    wl0 = I.single_cloud(n=300, sigma_um=0.4, z0_um=50.0, seed=4, img=32)
+    path = tmp_path / "cloud.txt"
+    carrier_io.save_carriers(str(path), wl0.xyz)
+    wl = carrier_io.load_carriers(str(path), img=32, seeds=[4])
+    res = run(gc, wl, gc.GC_FP64)
+    ref = O.Simulation(O.make_params(img_w=32, img_h=32), wl.xyz, wl.ev_off, wl.seeds, wl.img_origin)
+    ref.run()
+    assert np.array_equal(res["collect_step"], ref.collect_step)
+    assert np.array_equal(res["image"], ref.image)
+    assert np.abs(res["positions"] - ref.positions()).max() < 1e-4
