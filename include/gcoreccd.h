@@ -157,6 +157,29 @@ gc_status gc_positions(gc_sim *s, double *xyz);
 /* Device counters (host struct). */
 gc_status gc_get_stats(gc_sim *s, gc_stats *st);
 
+/* A checkpoint of a simulation, in caller-owned host buffers of the sizes
+ * given.  Because the diffusion vectors are counter-based (Philox keyed by
+ * the event seed, the carrier's index in its event and the step), this is the
+ * whole state: a restored run continues exactly as the uninterrupted one. */
+typedef struct {
+    double *xyz;                  /* [n][3] current positions, original order */
+    int32_t *collect_step;        /* [n] step of collection, -1 while active */
+    uint32_t *image;              /* [n_events][img_h][img_w] */
+    int64_t *off_image;           /* [n_events] */
+    int64_t step;                 /* time steps completed */
+    double pair_interactions;     /* counters of gc_stats, carried over */
+    double carrier_steps;
+} gc_state;
+
+/* Copy the state into `st` (all its pointers must be valid host buffers). */
+gc_status gc_save_state(gc_sim *s, gc_state *st);
+
+/* Replace the state of `s` by `st`.  `s` must hold the same carriers, events,
+ * seeds and image origins as the simulation the state was saved from
+ * (gc_load_carriers with the same arguments); GC_ERR_PARAM when a saved
+ * carrier is inconsistent (active but in the well, or beyond the back). */
+gc_status gc_restore_state(gc_sim *s, const gc_state *st);
+
 /* Eq. 6 on its own: the softened Coulomb field at every one of n carriers
  * from all n (one event), in V/cm.  xyz_dev: device [n][3] FP64 positions
  * (um); E_dev: device [n][3] FP64 output.  precision: gc_precision.  Runs on

@@ -754,6 +754,92 @@ gc_status gc_get_stats(gc_sim *s, gc_stats *out) {
     return GC_OK;
 }
 
+gc_status gc_save_state(gc_sim *s, gc_state *st) {
+    if (!s || !st || (s->n > 0 && (!st->xyz || !st->collect_step)) || !st->image || !st->off_image)
+        return GC_ERR_PARAM;
+    if (!s->loaded) return GC_ERR_STATE;
+    gc_status r = gc_positions(s, st->xyz);
+    if (r != GC_OK) return r;
+    r = gc_collect(s, nullptr, st->collect_step, nullptr, st->off_image, nullptr);
+    if (r != GC_OK) return r;
+    r = gc_image(s, st->image, 0);
+    if (r != GC_OK) return r;
+    r = read_ctrl(s);
+    if (r != GC_OK) return r;
+    st->step = s->h_ctrl->step;
+    st->pair_interactions = (double)s->h_ctrl->pair_interactions;
+    st->carrier_steps = (double)s->h_ctrl->carrier_steps;
+    return GC_OK;
+}
+
+gc_status gc_restore_state(gc_sim *s, const gc_state *st) {
+    if (!s || !st || (s->n > 0 && (!st->xyz || !st->collect_step)) || !st->image || !st->off_image)
+        return GC_ERR_PARAM;
+    if (!s->loaded) return GC_ERR_STATE;
+    if (st->step < 0 || st->step > s->p.max_steps) return GC_ERR_PARAM;
+    const int64_t n = s->n, E = s->E;
+    for (int64_t i = 0; i < n; ++i) {
+        const double z = st->xyz[3 * i + 2];
+        if (!is_finite(st->xyz[3 * i]) || !is_finite(st->xyz[3 * i + 1]) || !is_finite(z)) return GC_ERR_PARAM;
+        if (st->collect_step[i] < -1 || st->collect_step[i] > st->step) return GC_ERR_PARAM;
+        if (st->collect_step[i] < 0 && (z <= s->p.z_well_um || (s->p.reflect_back && z > s->p.thickness_um)))
+            return GC_ERR_PARAM;
+    }
+    GC_CUDA(cudaSetDevice(s->device));
+    Dev &d = s->dev;
+    cudaStream_t q = s->stream;
+    // the active list in the load order: internal events, ascending id within each
+    std::vector<int> ev_user(E), act(std::max<int64_t>(n, 1)), ioff(E + 1);
+    GC_CUDA(cudaMemcpy(ev_user.data(), d.ev_user, E * 4, cudaMemcpyDeviceToHost));
+    int pos = 0;
+    for (int64_t ie = 0; ie < E; ++ie) {
+        ioff[ie] = pos;
+        const int ue = ev_user[ie];
+        for (int64_t id = s->user_off[ue]; id < s->user_off[ue + 1]; ++id)
+            if (st->collect_step[id] < 0) act[pos++] = (int)id;
+    }
+    ioff[E] = pos;
+    std::vector<double> hx(std::max<int64_t>(n, 1)), hy(hx.size()), hz(hx.size());
+    for (int64_t i = 0; i < n; ++i) {
+        hx[i] = st->xyz[3 * i];
+        hy[i] = st->xyz[3 * i + 1];
+        hz[i] = st->xyz[3 * i + 2];
+    }
+    std::vector<unsigned long long> off(std::max<int64_t>(E, 1));
+    for (int64_t e = 0; e < E; ++e) off[e] = (unsigned long long)st->off_image[e];
+    const size_t img = (size_t)E * s->p.img_w * s->p.img_h;
+    GC_CUDA(cudaMemcpyAsync(d.px, hx.data(), n * 8, cudaMemcpyHostToDevice, q));
+    GC_CUDA(cudaMemcpyAsync(d.py, hy.data(), n * 8, cudaMemcpyHostToDevice, q));
+    GC_CUDA(cudaMemcpyAsync(d.pz, hz.data(), n * 8, cudaMemcpyHostToDevice, q));
+    GC_CUDA(cudaMemcpyAsync(d.collect_step, st->collect_step, n * 4, cudaMemcpyHostToDevice, q));
+    GC_CUDA(cudaMemcpyAsync(d.image, st->image, img * 4, cudaMemcpyHostToDevice, q));
+    GC_CUDA(cudaMemcpyAsync(d.off_image, off.data(), E * 8, cudaMemcpyHostToDevice, q));
+    GC_CUDA(cudaMemcpyAsync(d.act[0], act.data(), (size_t)pos * 4, cudaMemcpyHostToDevice, q));
+    GC_CUDA(cudaMemcpyAsync(d.ev_off[0], ioff.data(), (E + 1) * 4, cudaMemcpyHostToDevice, q));
+    GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, q));
+    GC_CUDA(cudaStreamSynchronize(q));
+    Ctrl c{};
+    c.step = st->step;
+    c.step_limit = LLONG_MAX;  // open for the rebuild pass
+    c.n_active = pos;
+    c.cur = 0;
+    c.pair_interactions = (unsigned long long)st->pair_interactions;
+    c.carrier_steps = (unsigned long long)st->carrier_steps;
+    *s->h_ctrl = c;
+    GC_CUDA(cudaMemcpyAsync(d.ctrl, s->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, q));
+    if (pos > 0) {
+        // the step-0 pass keeps every (consistent) active carrier and rebuilds
+        // the shadow, the event offsets and the pair work items
+        const bool f64 = fp64_mode(s);
+        GC_CUDA(launch_integrate(d, f64, true, s->integ_grid, q));
+        GC_CUDA(launch_compact(d, f64, s->integ_grid, q));
+        GC_CUDA(launch_finalize(d, true, q));
+    }
+    gc_status r = set_limit(s, st->step);
+    if (r != GC_OK) return r;
+    return read_ctrl(s);
+}
+
 gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um, double eps_si_rel,
                            int32_t precision, double *E_dev, void *cuda_stream) {
     if (n < 0 || n > (1LL << 30)) return GC_ERR_PARAM;

@@ -25,7 +25,7 @@ GC_FP64, GC_FP32, GC_FP32_KAHAN, GC_FP16X2 = 0, 1, 2, 3
 # Every symbol include/gcoreccd.h declares.
 EXPORTS = ("gc_default_params", "gc_create", "gc_load_carriers", "gc_run", "gc_collect",
            "gc_image", "gc_positions", "gc_get_stats", "gc_coulomb_field",
-           "gc_coulomb_field_noalloc", "gc_destroy",
+           "gc_coulomb_field_noalloc", "gc_save_state", "gc_restore_state", "gc_destroy",
            "gc_status_string", "gc_last_cuda_error", "gc_device_info")
 
 
@@ -73,6 +73,18 @@ class GcStats(ctypes.Structure):
         ("integrate_kernel_ms", ctypes.c_double),
         ("compact_kernel_ms", ctypes.c_double),
         ("timed_steps", ctypes.c_int64),
+    ]
+
+
+class GcState(ctypes.Structure):
+    _fields_ = [
+        ("xyz", ctypes.c_void_p),
+        ("collect_step", ctypes.c_void_p),
+        ("image", ctypes.c_void_p),
+        ("off_image", ctypes.c_void_p),
+        ("step", ctypes.c_int64),
+        ("pair_interactions", ctypes.c_double),
+        ("carrier_steps", ctypes.c_double),
     ]
 
 
@@ -124,6 +136,10 @@ def load():
         L.gc_coulomb_field.argtypes = [P, I64, ctypes.c_double, ctypes.c_double, I32, P, P]
         L.gc_coulomb_field_noalloc.restype = I32
         L.gc_coulomb_field_noalloc.argtypes = [P, I64, ctypes.c_double, ctypes.c_double, I32, P, P]
+        L.gc_save_state.restype = I32
+        L.gc_save_state.argtypes = [P, ctypes.POINTER(GcState)]
+        L.gc_restore_state.restype = I32
+        L.gc_restore_state.argtypes = [P, ctypes.POINTER(GcState)]
         L.gc_destroy.restype = None
         L.gc_destroy.argtypes = [P]
         L.gc_status_string.restype = ctypes.c_char_p
@@ -261,6 +277,25 @@ def gc_coulomb_field_noalloc(xyz_dev, n: int, softening_um: float, eps_si_rel: f
            "gc_coulomb_field_noalloc")
 
 
+def gc_save_state(sim, n: int, n_events: int, img_h: int, img_w: int) -> dict:
+    """Checkpoint as numpy arrays plus the step and the counters."""
+    arrs = dict(xyz=np.zeros((n, 3)), collect_step=np.zeros(n, dtype=np.int32),
+                image=np.zeros((n_events, img_h, img_w), dtype=np.uint32),
+                off_image=np.zeros(n_events, dtype=np.int64))
+    st = GcState(*(arrs[k].ctypes.data for k in ("xyz", "collect_step", "image", "off_image")), 0, 0.0, 0.0)
+    _check(load().gc_save_state(sim, ctypes.byref(st)), "gc_save_state")
+    arrs.update(step=st.step, pair_interactions=st.pair_interactions, carrier_steps=st.carrier_steps)
+    return arrs
+
+
+def gc_restore_state(sim, state: dict) -> None:
+    a = {k: np.ascontiguousarray(state[k], dtype=t) for k, t in
+         (("xyz", np.float64), ("collect_step", np.int32), ("image", np.uint32), ("off_image", np.int64))}
+    st = GcState(*(a[k].ctypes.data for k in ("xyz", "collect_step", "image", "off_image")),
+                 int(state["step"]), float(state["pair_interactions"]), float(state["carrier_steps"]))
+    _check(load().gc_restore_state(sim, ctypes.byref(st)), "gc_restore_state")
+
+
 def gc_destroy(sim) -> None:
     if sim:
         load().gc_destroy(sim)
@@ -297,6 +332,12 @@ class Simulation:
 
     def stats(self) -> dict:
         return gc_get_stats(self.handle)
+
+    def save_state(self) -> dict:
+        return gc_save_state(self.handle, self.n, self.n_events, self.params.img_h, self.params.img_w)
+
+    def restore_state(self, state: dict) -> None:
+        gc_restore_state(self.handle, state)
 
     def close(self):
         if self.handle:

@@ -359,3 +359,48 @@ def test_coulomb_off_lateral_spread_at_scale(gc):
         assert r["final_xy"][:, c].var() == pytest.approx(want, rel=tol)
     # the mean collection step is the drift time t(300 um) = 12.3143 ns (1231.4 steps)
     assert r["collect_step"].mean() == pytest.approx(1231.4, rel=5e-3)
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_resume_equals_uninterrupted(gc, precision):
+    """run(2k) is bit-identical to run(k) -> gc_save_state -> a new
+    simulation -> gc_restore_state -> run(k): the diffusion stream is
+    counter-based, so the checkpoint is the whole state."""
+    wl = I.single_cloud(n=900, sigma_um=0.4, z0_um=30.0, seed=21, img=32)
+    p = gc.gc_default_params(precision=precision, img_w=32, img_h=32, graph_steps=8, pair_R=4)
+    k = 150
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as a:
+        a.run(2 * k)
+        want = (a.positions(), a.collect()["collect_step"], a.image(), a.stats())
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as b:
+        b.run(k)
+        state = b.save_state()
+    assert state["step"] == k and np.any(state["collect_step"] > 0) and np.any(state["collect_step"] < 0)
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as c:
+        c.restore_state(state)
+        assert c.stats()["steps"] == k
+        c.run(k)
+        got = (c.positions(), c.collect()["collect_step"], c.image(), c.stats())
+    assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[1], want[1])
+    assert np.array_equal(got[2], want[2])
+    assert got[3]["steps"] == want[3]["steps"] == 2 * k
+    assert got[3]["pair_interactions"] == want[3]["pair_interactions"]
+    assert got[3]["carrier_steps"] == want[3]["carrier_steps"]
+
+
+def test_restore_rejects_inconsistent_state(gc):
+    wl = I.single_cloud(n=50, z0_um=20.0, img=16)
+    p = gc.gc_default_params(img_w=16, img_h=16)
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as s:
+        st = s.save_state()
+        bad = dict(st, xyz=st["xyz"].copy())
+        bad["xyz"][3, 2] = -1.0  # active but already in the well
+        with pytest.raises(gc.GcError):
+            s.restore_state(bad)
+        bad = dict(st, collect_step=st["collect_step"].copy())
+        bad["collect_step"][0] = 5  # collected after the saved step
+        with pytest.raises(gc.GcError):
+            s.restore_state(bad)
+        s.restore_state(st)  # the consistent one is accepted
+        assert s.run(-1)[0] == gc.GC_OK
