@@ -366,9 +366,9 @@ def test_resume_equals_uninterrupted(gc, precision):
     """run(2k) is bit-identical to run(k) -> gc_save_state -> a new
     simulation -> gc_restore_state -> run(k): the diffusion stream is
     counter-based, so the checkpoint is the whole state."""
-    wl = I.single_cloud(n=900, sigma_um=0.4, z0_um=30.0, seed=21, img=32)
+    wl = I.single_cloud(n=900, sigma_um=0.4, z0_um=80.0, seed=21, img=32)
     p = gc.gc_default_params(precision=precision, img_w=32, img_h=32, graph_steps=8, pair_R=4)
-    k = 150
+    k = 285
     with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as a:
         a.run(2 * k)
         want = (a.positions(), a.collect()["collect_step"], a.image(), a.stats())
@@ -384,7 +384,7 @@ def test_resume_equals_uninterrupted(gc, precision):
     assert np.array_equal(got[0], want[0])
     assert np.array_equal(got[1], want[1])
     assert np.array_equal(got[2], want[2])
-    assert got[3]["steps"] == want[3]["steps"] == 2 * k
+    assert got[3]["steps"] == want[3]["steps"] > k
     assert got[3]["pair_interactions"] == want[3]["pair_interactions"]
     assert got[3]["carrier_steps"] == want[3]["carrier_steps"]
 
