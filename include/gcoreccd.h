@@ -102,6 +102,9 @@ typedef struct {
     double integrate_kernel_ms;   /* with timing on: summed device time of the integrate kernel */
     double compact_kernel_ms;     /* with timing on: summed device time of the compaction kernel */
     int64_t timed_steps;          /* with timing on: steps whose kernels were timed */
+    int32_t device_loop;          /* 1: gc_run is one graph launch with a device-side loop
+                                     (conditional WHILE node over passes of graph_steps steps) */
+    int32_t reserved;
 } gc_stats;
 
 /* Defaults: the CCD of the X-ray and muon workloads (thickness 675 um,

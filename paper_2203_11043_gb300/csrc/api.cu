@@ -141,8 +141,9 @@ struct gc_sim {
     DevAllocs mem;
     Dev dev{};
     Ctrl *h_ctrl = nullptr;          // pinned mirror of the device control block
-    long long *h_limit = nullptr;    // pinned staging for step_limit
+    long long *h_limit = nullptr;    // pinned staging for step_limit and loop_last
     cudaGraphExec_t graph = nullptr;
+    bool graph_loops = false;        // the graph holds a device-side WHILE loop over K-step passes
     int integ_grid = 1;
     int launches_per_step = 0;
     long long part_cap_chunks = 1;   // j-chunks the partial buffer can hold
@@ -197,19 +198,19 @@ gc_status read_ctrl(gc_sim *s) {
 }
 
 gc_status set_limit(gc_sim *s, long long limit) {
-    *s->h_limit = limit;
-    GC_CUDA(cudaMemcpyAsync(&s->dev.ctrl->step_limit, s->h_limit, sizeof(long long),
+    s->h_limit[0] = limit;
+    s->h_limit[1] = -1;  // loop_last: the next device-side loop starts afresh
+    GC_CUDA(cudaMemcpyAsync(&s->dev.ctrl->step_limit, s->h_limit, 2 * sizeof(long long),
                             cudaMemcpyHostToDevice, s->stream));
     GC_CUDA(cudaStreamSynchronize(s->stream));
     return GC_OK;
 }
 
-gc_status capture_graph(gc_sim *s) {
-    if (s->graph) {
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-    }
-    if (!use_graph(s)) return GC_OK;
+// A graph of K time steps.  Preferred form: one WHILE conditional node whose
+// body is K steps plus the loop-condition kernel, so a whole gc_run is one
+// graph launch with no host round trip; otherwise a plain graph of K steps
+// that gc_run launches repeatedly.
+gc_status capture_plain_graph(gc_sim *s) {
     cudaGraph_t g = nullptr;
     GC_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     gc_status st = GC_OK;
@@ -224,6 +225,56 @@ gc_status capture_graph(gc_sim *s) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e);
     return GC_OK;
+}
+
+bool capture_loop_graph(gc_sim *s) {
+    cudaGraph_t g = nullptr, body = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    bool ok = false;
+    do {
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) break;
+        body = np.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(s->stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            break;
+        gc_status st = GC_OK;
+        for (int k = 0; k < s->p.graph_steps && st == GC_OK; ++k) st = enqueue_step(s, k);
+        const cudaError_t le = st == GC_OK ? launch_loop_cond(s->dev, h, s->stream) : cudaErrorUnknown;
+        cudaGraph_t out = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(s->stream, &out);
+        if (st != GC_OK || le != cudaSuccess || ee != cudaSuccess) break;
+        if (cudaGraphInstantiate(&s->graph, g, 0) != cudaSuccess) break;
+        ok = true;
+    } while (0);
+    cudaGraphDestroy(g);
+    if (!ok) {
+        if (s->graph) cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+        cudaGetLastError();  // clear a failed attempt; the plain graph is used instead
+    }
+    return ok;
+}
+
+gc_status capture_graph(gc_sim *s) {
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    s->graph_loops = false;
+    if (!use_graph(s)) return GC_OK;
+    if (capture_loop_graph(s)) {
+        s->graph_loops = true;
+        return GC_OK;
+    }
+    return capture_plain_graph(s);
 }
 
 // Pick R (and the grid and j-chunk that follow from it) for the FP32 pair
@@ -392,7 +443,7 @@ gc_status gc_create(const gc_params *p, void *cuda_stream, gc_sim **out) {
             s->own_stream = true;
         }
         if ((e = cudaMallocHost((void **)&s->h_ctrl, sizeof(Ctrl))) != cudaSuccess) { st = cuda_fail(e); break; }
-        if ((e = cudaMallocHost((void **)&s->h_limit, sizeof(long long))) != cudaSuccess) { st = cuda_fail(e); break; }
+        if ((e = cudaMallocHost((void **)&s->h_limit, 2 * sizeof(long long))) != cudaSuccess) { st = cuda_fail(e); break; }
         std::memset(s->h_ctrl, 0, sizeof(Ctrl));
     } while (0);
     if (st != GC_OK) {
@@ -636,7 +687,12 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
             }
             return GC_OK;
         };
-        if (steps >= 0) {
+        if (s->graph_loops) {
+            // the device-side loop runs to the limit (or completion) in one launch
+            GC_CUDA(cudaGraphLaunch(s->graph, s->stream));
+            r = read_ctrl(s);
+            if (r != GC_OK) return r;
+        } else if (steps >= 0) {
             // known step count: enqueue everything, synchronise once
             for (long long k = 0; k < (want + K - 1) / K; ++k) {
                 r = launch_one();
@@ -751,6 +807,7 @@ gc_status gc_get_stats(gc_sim *s, gc_stats *out) {
     out->integrate_kernel_ms = s->integ_ms;
     out->compact_kernel_ms = s->compact_ms;
     out->timed_steps = s->timed_steps;
+    out->device_loop = s->graph_loops ? 1 : 0;
     return GC_OK;
 }
 

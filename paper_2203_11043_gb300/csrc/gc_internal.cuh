@@ -29,6 +29,7 @@ constexpr float kSentinel = 1.0e15f; // padding position: its Eq. 6 term rounds 
 struct Ctrl {
     long long step;          // time steps completed
     long long step_limit;    // stop when step reaches this (set by the host)
+    long long loop_last;     // step seen by the previous pass of a device-side loop
     int n_active;            // active carriers at the start of the next step
     int cur;                 // which of the double-buffered active lists is current
     int items_total;         // pair work items for the next step

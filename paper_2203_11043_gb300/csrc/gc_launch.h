@@ -17,6 +17,10 @@ cudaError_t launch_pair(const Dev &d, int precision, int newton, cudaStream_t st
 cudaError_t launch_integrate(const Dev &d, bool fp64, bool init, int grid, cudaStream_t st);
 cudaError_t launch_compact(const Dev &d, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st);
+// Device-side loop condition of a captured WHILE graph node: continue while
+// carriers are active, the step limit is not reached and the last pass made
+// progress (so the loop always ends).
+cudaError_t launch_loop_cond(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st);
 // Recompute the pair work items from the current active offsets (after the
 // pair-kernel shape changes).
 cudaError_t launch_build_items(const Dev &d, cudaStream_t st);

@@ -357,6 +357,14 @@ __global__ void __launch_bounds__(kChunkThreads) finalize_kernel(Dev d) {
     }
 }
 
+__global__ void loop_cond_kernel(Dev d, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Ctrl *c = d.ctrl;
+    const bool go = c->n_active > 0 && c->step < c->step_limit && c->step != c->loop_last;
+    c->loop_last = c->step;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // Items only (no counters, no buffer flip): used after the pair shape changes.
 __global__ void __launch_bounds__(kChunkThreads) build_items_kernel(Dev d) {
     __shared__ long long s_warp[33];
@@ -440,6 +448,11 @@ cudaError_t launch_compact(const Dev &d, bool fp64, int grid, cudaStream_t st) {
 cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st) {
     if (init) finalize_kernel<true><<<1, kChunkThreads, 0, st>>>(d);
     else finalize_kernel<false><<<1, kChunkThreads, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_cond(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st) {
+    loop_cond_kernel<<<1, 32, 0, st>>>(d, h);
     return cudaGetLastError();
 }
 

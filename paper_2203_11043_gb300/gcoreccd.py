@@ -73,6 +73,8 @@ class GcStats(ctypes.Structure):
         ("integrate_kernel_ms", ctypes.c_double),
         ("compact_kernel_ms", ctypes.c_double),
         ("timed_steps", ctypes.c_int64),
+        ("device_loop", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

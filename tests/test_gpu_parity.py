@@ -244,6 +244,24 @@ def test_graph_equals_eager_and_split_runs(gc):
         assert np.array_equal(o[3], outs[0][3])
 
 
+def test_device_side_loop_is_used_and_matches_eager(gc):
+    """With graphs, gc_run is one launch of a device-side WHILE loop; it
+    stops exactly at the requested step and when every carrier is in."""
+    wl = I.single_cloud(n=500, sigma_um=0.4, z0_um=40.0, seed=17, img=32)
+    res = []
+    for gs in (0, 7):
+        p = gc.gc_default_params(precision=2, img_w=32, img_h=32, graph_steps=gs, pair_R=4)
+        with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+            assert sim.stats()["device_loop"] == (1 if gs else 0)
+            assert sim.run(10) == (gc.GC_OK, 10)   # 10 is not a multiple of 7
+            assert sim.stats()["steps"] == 10
+            st, done = sim.run(-1)
+            assert st == gc.GC_OK and sim.stats()["n_active"] == 0
+            res.append((10 + done, sim.positions(), sim.collect()["collect_step"]))
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])
+
+
 def test_max_steps_incomplete_and_counts(gc):
     wl = I.single_cloud(n=200, z0_um=300.0)
     p = gc.gc_default_params(precision=2, img_w=32, img_h=32, max_steps=100)
