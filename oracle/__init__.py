@@ -64,6 +64,9 @@ class OrcParams(ctypes.Structure):
         ("pixel_um", ctypes.c_double),
         ("img_w", ctypes.c_int32),
         ("img_h", ctypes.c_int32),
+        ("stored_charge", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("stored_z_um", ctypes.c_double),
     ]
 
 
@@ -116,6 +119,8 @@ def lib():
             L.orc_step_targets.argtypes = [ctypes.POINTER(OrcParams), P, P, P, P,
                                            ctypes.c_int64, P, ctypes.c_int64,
                                            ctypes.c_uint64, ctypes.c_uint64, P]
+            L.orc_stored_field.restype = None
+            L.orc_stored_field.argtypes = [ctypes.POINTER(OrcParams), P, P, P, ctypes.c_int64, P]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
             _lib = L
@@ -130,7 +135,7 @@ def _ptr(a: np.ndarray):
 DEFAULTS = dict(thickness_um=675.0, z_well_um=0.0, a1=2.0, a2=1500.0, T=140.0,
                 eps_si_rel=11.7, softening_um=0.01, dt_s=1e-11, max_steps=100000,
                 coulomb=1, diffusion=1, reflect_back=1, pixel_um=15.0,
-                img_w=32, img_h=32)
+                img_w=32, img_h=32, stored_charge=0, pad=0, stored_z_um=0.0)
 
 
 def make_params(**kw) -> OrcParams:
@@ -255,6 +260,16 @@ def step_targets(params: OrcParams, xyz, src, targets, seed: int, step: int) -> 
     lib().orc_step_targets(ctypes.byref(params), _ptr(x), _ptr(y), _ptr(z), _ptr(src),
                            len(src), _ptr(tg), len(tg), int(seed), int(step), _ptr(out))
     return out
+
+
+def stored_field(params: OrcParams, image, origin, xyz) -> np.ndarray:
+    """Field in V/cm at points xyz [m, 3] from the charge stored in one event's image."""
+    img = np.ascontiguousarray(image, dtype=np.uint32)
+    org = np.ascontiguousarray(origin, dtype=np.float64).reshape(2)
+    pts = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    E = np.zeros((len(pts), 3))
+    lib().orc_stored_field(ctypes.byref(params), _ptr(img), _ptr(org), _ptr(pts), len(pts), _ptr(E))
+    return E
 
 
 def num_threads() -> int:

@@ -166,6 +166,41 @@ static void advance_one(const orc_params *p, double Vth, double x, double y, dou
     out[2] = zn;
 }
 
+/* Field of the charge stored in one event's image at one point (Sec. 1:
+ * charge already in a pixel deflects the charges that follow): pixel (ix, iy)
+ * with count q is q charges at (ox + (ix + 1/2) p, oy + (iy + 1/2) p,
+ * stored_z), each with the softened field of Eq. 6. */
+static void stored_field_at(const orc_params *p, const uint32_t *img, const double origin[2],
+                            double x, double y, double z, double K, double E[3]) {
+    const double eps2 = p->softening_um * p->softening_um;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t iy = 0; iy < p->img_h; ++iy) {
+        for (int64_t ix = 0; ix < p->img_w; ++ix) {
+            const uint32_t q = img[iy * p->img_w + ix];
+            if (q == 0) continue;
+            double cx = origin[0] + ((double)ix + 0.5) * p->pixel_um;
+            double cy = origin[1] + ((double)iy + 0.5) * p->pixel_um;
+            double rx = x - cx, ry = y - cy, rz = z - p->stored_z_um;
+            double r2 = rx * rx + ry * ry + rz * rz + eps2;
+            double denom = r2 * sqrt(r2);
+            sx += (double)q * (rx / denom);
+            sy += (double)q * (ry / denom);
+            sz += (double)q * (rz / denom);
+        }
+    }
+    E[0] = K * sx;
+    E[1] = K * sy;
+    E[2] = K * sz;
+}
+
+void orc_stored_field(const orc_params *p, const uint32_t *img, const double origin[2],
+                      const double *xyz, int64_t m, double *E) {
+    const double K = orc_coulomb_K(p->eps_si_rel);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < m; ++t)
+        stored_field_at(p, img, origin, xyz[3 * t], xyz[3 * t + 1], xyz[3 * t + 2], K, &E[3 * t]);
+}
+
 /* 2-D histogram with half-open bins [k p, (k+1) p) measured from the event's
  * image origin (Fig. 5). */
 static void bin_collected(const orc_params *p, orc_state *s, int64_t e, double x, double y) {
@@ -230,6 +265,19 @@ int64_t orc_run(const orc_params *p, orc_state *s, int64_t steps) {
                                   p->softening_um, K, Ec);
             else
                 memset(Ec, 0, sizeof(double) * 3 * (size_t)na);
+            /* plus the field of the charge already stored in the event's pixels */
+            if (p->stored_charge) {
+                const uint32_t *img = s->image + (size_t)e * p->img_w * p->img_h;
+#pragma omp parallel for schedule(static)
+                for (int64_t k = 0; k < na; ++k) {
+                    const int64_t i = active[k];
+                    double Es[3];
+                    stored_field_at(p, img, &s->img_origin[2 * e], s->x[i], s->y[i], s->z[i], K, Es);
+                    Ec[3 * k] += Es[0];
+                    Ec[3 * k + 1] += Es[1];
+                    Ec[3 * k + 2] += Es[2];
+                }
+            }
             /* every carrier moves from the start-of-step state (synchronous update) */
 #pragma omp parallel for schedule(static)
             for (int64_t k = 0; k < na; ++k) {

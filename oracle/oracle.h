@@ -44,6 +44,9 @@ typedef struct {
     int32_t reflect_back;  /* reflect at z = thickness */
     double pixel_um;       /* pixel pitch of the output histogram (Fig. 5: 15 um) */
     int32_t img_w, img_h;  /* image size in pixels */
+    int32_t stored_charge; /* 1: charge already collected in a pixel sources a field (Sec. 1) */
+    int32_t pad;
+    double stored_z_um;    /* depth of the stored-charge points (pixel centres at this z) */
 } orc_params;
 
 /* Simulation state.  All arrays are caller-owned; positions are updated in
@@ -97,6 +100,13 @@ int orc_init(const orc_params *p, orc_state *s);
  * carrier is active or max_steps is reached.  Returns the steps executed,
  * or -1 on invalid arguments. */
 int64_t orc_run(const orc_params *p, orc_state *s, int64_t steps);
+
+/* Field in V/cm at the m points xyz[3t..3t+2] from the charge stored in one
+ * event's image (img [img_h][img_w], lower-left corner origin[2]): each pixel
+ * with count q acts as q point charges at its centre at depth stored_z_um,
+ * with the softened form of Eq. 6; pixels are summed in index order. */
+void orc_stored_field(const orc_params *p, const uint32_t *img, const double origin[2],
+                      const double *xyz, int64_t m, double *E);
 
 /* One step for a sample of carriers of a single event whose carriers are
  * x, y, z[0..) (so an index is also the index within the event), without

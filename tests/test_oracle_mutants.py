@@ -35,6 +35,9 @@ MUTANTS = {
     "reflection_clamp": ("zn = 2.0 * p->thickness_um - zn;", "zn = p->thickness_um;"),
     "coulomb_K_missing_4pi": ("(4.0 * ORC_PI * ORC_EPS0 * eps_rel)", "(ORC_EPS0 * eps_rel)"),
     "thermal_voltage_inverted": ("return ORC_KB * T / ORC_Q;", "return ORC_Q * T / ORC_KB;"),
+    "stored_pixel_corner": ("double cx = origin[0] + ((double)ix + 0.5) * p->pixel_um;",
+                            "double cx = origin[0] + ((double)ix) * p->pixel_um;"),
+    "stored_charge_unweighted": ("sx += (double)q * (rx / denom);", "sx += (rx / denom);"),
 }
 
 

@@ -330,3 +330,89 @@ def test_event_independent_of_batch():
     assert np.array_equal(alone.positions(), both.positions()[25:])
     assert np.array_equal(alone.collect_step, both.collect_step[25:])
     assert np.array_equal(alone.image[0], both.image[1])
+
+
+# ---- stored charge (Sec. 1: charge already in a pixel deflects later charges) -------------
+
+def _stored_image():
+    img = np.zeros((4, 5), dtype=np.uint32)
+    img[1, 2], img[3, 0], img[0, 4] = 7, 2, 5
+    return img, np.array([-30.0, -20.0])
+
+
+def test_stored_field_is_minus_gradient_of_its_potential():
+    """The stored-charge field is minus the gradient (central differences) of
+    K sum_p q_p / sqrt(|r - c_p|^2 + eps^2) over the pixel centres c_p at
+    (ox + (ix + 1/2) p, oy + (iy + 1/2) p, stored_z)."""
+    p = O.make_params(img_w=5, img_h=4, pixel_um=15.0, softening_um=0.05, stored_z_um=-0.5)
+    img, org = _stored_image()
+    K = O.coulomb_K(11.7)
+    iy, ix = np.nonzero(img)
+    centres = np.stack([org[0] + (ix + 0.5) * 15.0, org[1] + (iy + 0.5) * 15.0,
+                        np.full(len(ix), -0.5)], axis=1)
+    q = img[iy, ix].astype(float)
+
+    def phi(r):
+        d = r[None, :] - centres
+        return K * np.sum(q / np.sqrt((d * d).sum(1) + 0.05 ** 2))
+
+    pts = np.array([[3.0, -1.0, 4.0], [-22.0, 27.0, 0.7], [40.0, -15.0, 30.0]])
+    E = O.stored_field(p, img, org, pts)
+    h = 1e-5
+    for t, r in enumerate(pts):
+        for c in range(3):
+            rp, rm = r.copy(), r.copy()
+            rp[c] += h
+            rm[c] -= h
+            assert E[t, c] == pytest.approx(-(phi(rp) - phi(rm)) / (2 * h), rel=2e-6, abs=1e-9)
+
+
+def test_stored_field_equals_point_sources_at_pixel_centres():
+    """The same field as Eq. 6 from q_p carriers placed at each pixel centre."""
+    p = O.make_params(img_w=5, img_h=4, pixel_um=15.0, stored_z_um=0.0)
+    img, org = _stored_image()
+    iy, ix = np.nonzero(img)
+    src = np.concatenate([np.tile([[org[0] + (a + 0.5) * 15.0, org[1] + (b + 0.5) * 15.0, 0.0]],
+                                  (int(img[b, a]), 1)) for b, a in zip(iy, ix)])
+    pts = np.array([[1.0, 2.0, 3.0], [-10.0, 5.0, 0.2]])
+    E = O.stored_field(p, img, org, pts)
+    allp = np.concatenate([pts, src])
+    ref = O.coulomb_field(allp, targets=[0, 1], src=np.arange(2, len(allp)))
+    np.testing.assert_allclose(E, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_stored_charge_one_step_closed_form_and_off_switch():
+    """A hole above a pixel holding q collected holes (no depletion field, no
+    diffusion) moves by 1e4 mu(|E|) E dt with E the stored-charge field; with
+    stored_charge = 0 the collected charge exerts nothing."""
+    K = O.coulomb_K(11.7)
+    q = 40
+    # q holes start in the well under pixel (1, 1) of a 3 x 3 image; one hole at 2 um above it
+    centre = np.array([-7.5, -7.5]) + 1.5 * 15.0
+    xyz = np.concatenate([np.tile([[centre[0], centre[1], -0.1]], (q, 1)),
+                          [[centre[0] + 1.0, centre[1], 2.0]]])
+    for stored in (0, 1):
+        p = O.make_params(a1=0.0, a2=0.0, diffusion=0, coulomb=1, img_w=3, img_h=3, pixel_um=15.0,
+                          stored_charge=stored, stored_z_um=-0.1, z_well_um=-0.05)
+        sim = O.Simulation(p, xyz, img_origin=[[-7.5, -7.5]])
+        assert sim.image[0, 1, 1] == q  # collected at step 0
+        sim.run(1)
+        d = np.array([1.0, 0.0, 2.1])
+        E = stored * K * q * d / (d @ d + 1e-4) ** 1.5
+        mu = O.mobility(np.linalg.norm(E), 140.0)
+        want = np.array([centre[0] + 1.0, centre[1], 2.0]) + 1e4 * mu * E * 1e-11
+        np.testing.assert_allclose(sim.positions()[-1], want, rtol=1e-12, atol=1e-12)
+
+
+def test_stored_charge_broadens_the_image():
+    """Sec. 1: charge already stored deflects the charges that follow, so a
+    dense cloud ends wider with the stored-charge field on."""
+    rng = np.random.default_rng(2)
+    xyz = rng.normal(size=(600, 3)) * 0.3 + np.array([0.0, 0.0, 40.0])
+    sig = []
+    for stored in (0, 1):
+        p = O.make_params(img_w=16, img_h=16, pixel_um=3.0, stored_charge=stored, stored_z_um=0.0)
+        sim = O.Simulation(p, xyz, img_origin=[[-24.0, -24.0]])
+        sim.run()
+        sig.append(np.hypot(sim.x.std(), sim.y.std()))
+    assert sig[1] > sig[0] * 1.001
