@@ -251,7 +251,7 @@ def to_completion(args):
 
     def timed_run(w):
         p = gc.gc_default_params(precision=prec, img_w=w.img_w, img_h=w.img_h, pair_R=args.pair_R,
-                                 coulomb=args.coulomb)
+                                 coulomb=args.coulomb, stored_charge=args.stored_charge)
         with gc.Simulation(p, w.xyz, w.ev_off, w.seeds, w.img_origin, stream=stream.cuda_stream) as s:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -267,6 +267,7 @@ def to_completion(args):
             "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": 1e3 * secs / max(steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "mode": "to completion", "coulomb": args.coulomb,
+            "stored_charge": args.stored_charge,
             "config": {"workload": WORKLOADS[args.workload], "n_carriers": wl.n,
                        "events": wl.n_events, "pair_R": stats["pair_variant"],
                        "jchunk": stats["jchunk"], "pair_blocks": stats["pair_blocks"]},
@@ -309,6 +310,8 @@ def main():
                     help="time one run until every hole is collected (graphs, no per-step flush)")
     ap.add_argument("--coulomb", type=int, default=1, choices=[0, 1],
                     help="0 runs the O(N) Coulomb-off path (metric: carrier-steps/s)")
+    ap.add_argument("--stored-charge", type=int, default=0, choices=[0, 1],
+                    help="with --to-completion: 1 adds the field of the charge stored in the pixels")
     ap.add_argument("--per-event", type=int, default=0,
                     help="with --to-completion: also run the first M events one simulation each")
     args = ap.parse_args()

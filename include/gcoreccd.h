@@ -82,6 +82,12 @@ typedef struct {
     int32_t pair_R;        /* carriers per thread in the FP32 pair kernel (2, 4, 8); 0 = automatic */
     int32_t timing;        /* 1: bracket every pair-kernel launch with CUDA events (gc_get_stats);
                               steps are then launched one by one instead of as graphs */
+    int32_t stored_charge; /* 1: charge already collected in a pixel sources a field on the holes
+                              still moving (Sec. 1): pixel count q = q charges at the pixel centre
+                              at depth stored_z_um, softened as in Eq. 6; the image at the start of
+                              each step; off-image charge is not stored */
+    int32_t reserved;
+    double stored_z_um;    /* depth of the stored-charge points */
 } gc_params;
 
 typedef struct gc_sim gc_sim;

@@ -51,7 +51,7 @@ gc_status validate(const gc_params *p) {
     if (p->precision < GC_FP64 || p->precision > GC_FP16X2) return GC_ERR_PARAM;
     if (p->precision == GC_FP16X2 && p->newton) return GC_ERR_PARAM;
     const double v[] = {p->thickness_um, p->z_well_um, p->a1_V_cm_um, p->a2_V_cm, p->T_K,
-                        p->eps_si_rel, p->softening_um, p->dt_s, p->pixel_um};
+                        p->eps_si_rel, p->softening_um, p->dt_s, p->pixel_um, p->stored_z_um};
     for (double x : v)
         if (!is_finite(x)) return GC_ERR_PARAM;
     if (!(p->thickness_um > 0) || !(p->T_K > 0) || !(p->dt_s > 0) || !(p->pixel_um > 0))
@@ -60,10 +60,12 @@ gc_status validate(const gc_params *p) {
     if (p->max_steps < 0 || p->max_steps > INT_MAX) return GC_ERR_PARAM;
     if (p->img_w <= 0 || p->img_h <= 0 || (int64_t)p->img_w * p->img_h > (1 << 26))
         return GC_ERR_PARAM;
-    if (p->coulomb && (!(p->softening_um > 0) || !(p->eps_si_rel > 0))) return GC_ERR_PARAM;
+    if ((p->coulomb || p->stored_charge) && (!(p->softening_um > 0) || !(p->eps_si_rel > 0)))
+        return GC_ERR_PARAM;
     if (p->graph_steps < 0 || p->graph_steps > 4096) return GC_ERR_PARAM;
     if (p->jchunk < 0) return GC_ERR_PARAM;
-    if ((p->coulomb | p->diffusion | p->reflect_back | p->autotune | p->newton | p->timing) & ~1)
+    if ((p->coulomb | p->diffusion | p->reflect_back | p->autotune | p->newton | p->timing |
+         p->stored_charge) & ~1)
         return GC_ERR_PARAM;
     if (p->pair_R != 0 && p->pair_R != 2 && p->pair_R != 4 && p->pair_R != 8) return GC_ERR_PARAM;
     return GC_OK;
@@ -91,6 +93,8 @@ Phys make_phys(const gc_params &p) {
     ph.coulomb = p.coulomb;
     ph.diffusion = p.diffusion;
     ph.reflect = p.reflect_back;
+    ph.stored = p.stored_charge;
+    ph.stored_z = p.stored_z_um;
     return ph;
 }
 
@@ -183,6 +187,7 @@ gc_status enqueue_step(gc_sim *s, int k) {
     if (timed) GC_CUDA(cudaEventRecord(s->ev_a[k], s->stream));
     if (s->phys.coulomb) GC_CUDA(launch_pair(s->dev, s->p.precision, s->p.newton, s->stream));
     if (timed) GC_CUDA(cudaEventRecord(s->ev_b[k], s->stream));
+    if (s->phys.stored) GC_CUDA(launch_occupied_pixels(s->dev, s->stream));
     GC_CUDA(launch_integrate(s->dev, f64, false, s->integ_grid, s->stream));
     if (timed) GC_CUDA(cudaEventRecord(s->ev_c[k], s->stream));
     GC_CUDA(launch_compact(s->dev, f64, s->integ_grid, s->stream));
@@ -568,6 +573,13 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     if (s->p.precision == GC_FP16X2) {
         GC_ALLOC(d.ev_ext[0], E * 4) GC_ALLOC(d.ev_ext[1], E * 4)
     }
+    std::vector<int> occ_off(E + 1, 0);  // stored charge: per-event occupied-pixel capacity
+    for (int64_t ie = 0; ie < E; ++ie)
+        occ_off[ie + 1] = occ_off[ie] + (int)std::min<long long>((long long)s->p.img_w * s->p.img_h, sizes[ie]);
+    if (s->phys.stored) {
+        GC_ALLOC(d.occ_pix, (size_t)std::max(occ_off[E], 1) * 4)
+        GC_ALLOC(d.occ_off, (E + 1) * 4) GC_ALLOC(d.occ_cnt, E * 4)
+    }
     GC_ALLOC(d.keepmask, nchunk * (kChunk / 32) * 4) GC_ALLOC(d.chunk_cnt, nchunk * 4)
     GC_ALLOC(d.ev_off[0], (E + 1) * 4) GC_ALLOC(d.ev_off[1], (E + 1) * 4)
     GC_ALLOC(d.ev_collected_now, E * 4) GC_ALLOC(d.item_base, (E + 1) * 4)
@@ -597,6 +609,10 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     GC_CUDA(cudaMemcpyAsync(d.img_origin, iorig.data(), E * 16, cudaMemcpyHostToDevice, st));
     GC_CUDA(cudaMemcpyAsync(d.ev_user, ev_user.data(), E * 4, cudaMemcpyHostToDevice, st));
     GC_CUDA(cudaMemcpyAsync(d.ev_first, ev_first.data(), E * 4, cudaMemcpyHostToDevice, st));
+    if (d.occ_off) {
+        GC_CUDA(cudaMemcpyAsync(d.occ_off, occ_off.data(), (E + 1) * 4, cudaMemcpyHostToDevice, st));
+        GC_CUDA(cudaMemsetAsync(d.occ_cnt, 0, E * 4, st));
+    }
     GC_CUDA(cudaMemsetAsync(d.collect_step, 0xFF, N * 4, st));
     GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, st));
     GC_CUDA(cudaMemsetAsync(d.image, 0, img * 4, st));
@@ -629,7 +645,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     if (r != GC_OK) return r;
     r = read_ctrl(s);
     if (r != GC_OK) return r;
-    s->launches_per_step = (s->phys.coulomb ? 1 : 0) + 3;
+    s->launches_per_step = (s->phys.coulomb ? 1 : 0) + (s->phys.stored ? 1 : 0) + 3;
     if (s->p.timing) {
         for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
             v->resize(1);

@@ -54,6 +54,8 @@ struct Phys {
     double pixel;            // pixel pitch, um
     int img_w, img_h;
     int coulomb, diffusion, reflect;
+    int stored;              // stored-charge field on (Sec. 1)
+    double stored_z;         // depth of the stored-charge points, um
 };
 
 // Pair-kernel work decomposition, fixed at load time.
@@ -86,6 +88,9 @@ struct Dev {
     int *ev_user;            // internal -> caller event index
     int *ev_first;           // internal event -> id of its first carrier
     unsigned *image;         // [E_user][H][W]
+    int *occ_pix;            // stored charge: occupied pixel indices, per event in index order
+    int *occ_off;            // [E+1] capacity offsets of each event's occupied-pixel list
+    int *occ_cnt;            // [E] occupied pixels this step
     unsigned long long *off_image;
     Ctrl *ctrl;
     int n_total;

@@ -17,6 +17,9 @@ cudaError_t launch_pair(const Dev &d, int precision, int newton, cudaStream_t st
 cudaError_t launch_integrate(const Dev &d, bool fp64, bool init, int grid, cudaStream_t st);
 cudaError_t launch_compact(const Dev &d, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st);
+// Stored charge (Sec. 1): the occupied pixels of each event's image, in
+// pixel-index order, as the field sources of the coming integrate.
+cudaError_t launch_occupied_pixels(const Dev &d, cudaStream_t st);
 // Device-side loop condition of a captured WHILE graph node: continue while
 // carriers are active, the step limit is not reached and the last pass made
 // progress (so the loop always ends).

@@ -50,6 +50,76 @@ __device__ __forceinline__ void normals32(uint4 b, float n[3]) {
     n[2] = r1 * cospif(2.0f * ((float)b.w * s));
 }
 
+// ---- stored charge (Sec. 1) ----------------------------------------------------------
+// Field of the charge stored in event e's pixels at the carrier whose shadow
+// position (relative to the event origin o) is r: pixel (ix, iy) with count q
+// is q charges at (img_origin + (i + 1/2) p, stored_z), softened as in Eq. 6,
+// summed in pixel-index order.  Unscaled (multiply by K).
+template <typename T>
+__device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, T rz0, T &sx, T &sy,
+                                             T &sz) {
+    const Phys &ph = d.phys;
+    const int eu = d.ev_user[e];
+    const unsigned *img = d.image + (long long)eu * ph.img_h * ph.img_w;
+    // pixel (0, 0) centre relative to the event origin
+    const T cx0 = (T)(d.img_origin[2 * e] + 0.5 * ph.pixel - d.ev_origin[3 * e]);
+    const T cy0 = (T)(d.img_origin[2 * e + 1] + 0.5 * ph.pixel - d.ev_origin[3 * e + 1]);
+    const T dz = rz0 - (T)(ph.stored_z - d.ev_origin[3 * e + 2]);
+    const T pix = (T)ph.pixel, eps2 = (T)ph.eps2;
+    const int *occ = d.occ_pix + d.occ_off[e];
+    const int cnt = d.occ_cnt[e];
+    sx = sy = sz = (T)0;
+    for (int k = 0; k < cnt; ++k) {
+        const int pidx = occ[k];
+        const int iy = pidx / ph.img_w, ix = pidx - iy * ph.img_w;
+        const T q = (T)img[pidx];
+        const T dx = rx0 - (cx0 + (T)ix * pix), dy = ry0 - (cy0 + (T)iy * pix);
+        const T r2 = dx * dx + dy * dy + dz * dz + eps2;
+        const T w = q / (r2 * sqrt(r2));
+        sx += dx * w;
+        sy += dy * w;
+        sz += dz * w;
+    }
+}
+
+// One block per event: the occupied pixels of its image in index order
+// (warp ballot + block prefix), for the stored-charge field of this step.
+__global__ void __launch_bounds__(kChunkThreads) occupied_pixels_kernel(Dev d) {
+    __shared__ int s_warp[kChunkThreads / 32];
+    __shared__ int s_base;
+    Ctrl *c = d.ctrl;
+    if (step_skipped(c)) return;
+    const int npix = d.phys.img_w * d.phys.img_h;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = blockIdx.x; e < d.n_events; e += gridDim.x) {
+        const unsigned *img = d.image + (long long)d.ev_user[e] * npix;
+        int *out = d.occ_pix + d.occ_off[e];
+        const int cap = d.occ_off[e + 1] - d.occ_off[e];
+        if (threadIdx.x == 0) s_base = 0;
+        __syncthreads();
+        for (int b0 = 0; b0 < npix; b0 += kChunkThreads) {
+            const int pidx = b0 + threadIdx.x;
+            const bool occ = pidx < npix && img[pidx] != 0u;
+            const unsigned m = __ballot_sync(0xffffffffu, occ);
+            if (lane == 0) s_warp[warp] = __popc(m);
+            __syncthreads();
+            int before = s_base;
+            for (int w = 0; w < warp; ++w) before += s_warp[w];
+            const int k = before + __popc(m & ((1u << lane) - 1u));
+            if (occ && k < cap) out[k] = pidx;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int t = 0;
+                for (int w = 0; w < kChunkThreads / 32; ++w) t += s_warp[w];
+                s_base += t;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) d.occ_cnt[e] = min(s_base, cap);
+        __syncthreads();
+    }
+}
+
 // ---- per-slot step -------------------------------------------------------------------
 // Returns true when the carrier stays active.
 template <bool F64, bool INIT>
@@ -79,6 +149,23 @@ __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long 
             ex *= ph.K;
             ey *= ph.K;
             ez *= ph.K;
+        }
+        if (ph.stored) {  // the charge already in the event's pixels (Sec. 1)
+            if (F64) {
+                const double4_32a r = d.sh64[p];
+                double sx, sy, sz;
+                stored_field<double>(d, e, r.x, r.y, r.z, sx, sy, sz);
+                ex += ph.K * sx;
+                ey += ph.K * sy;
+                ez += ph.K * sz;
+            } else {
+                const float4 r = d.sh32[p];
+                float sx, sy, sz;
+                stored_field<float>(d, e, r.x, r.y, r.z, sx, sy, sz);
+                ex += ph.K * (double)sx;
+                ey += ph.K * (double)sy;
+                ez += ph.K * (double)sz;
+            }
         }
         ez += ph.a1 * z - ph.a2;  // Eq. 1
         double dx, dy, dz;
@@ -236,7 +323,7 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
                 const int q = base + s_wpre[m] + __popc(w & ((1u << lane) - 1u));
                 const int id = src[p];
                 dst[q] = id;
-                if (d.phys.coulomb) {  // the O(N) path reads no shadow
+                if (d.phys.coulomb || d.phys.stored) {  // the O(N) path reads no shadow
                     e = d.ev_of_id[id];
                     const double ox = d.ev_origin[3 * e], oy = d.ev_origin[3 * e + 1],
                                  oz = d.ev_origin[3 * e + 2];
@@ -250,7 +337,7 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
                     }
                 }
             }
-            if (!F64 && d.ev_ext[0] && d.phys.coulomb) {  // FP16x2 form: per-event max |coordinate|
+            if (!F64 && d.ev_ext[0] && (d.phys.coulomb || d.phys.stored)) {  // FP16x2: max |coordinate|
                 unsigned *ext = d.ev_ext[cur ^ 1];
                 const unsigned lead = __ffs(__ballot_sync(0xffffffffu, keep));
                 if (lead) {
@@ -453,6 +540,11 @@ cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st) {
 
 cudaError_t launch_loop_cond(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st) {
     loop_cond_kernel<<<1, 32, 0, st>>>(d, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_occupied_pixels(const Dev &d, cudaStream_t st) {
+    occupied_pixels_kernel<<<min(d.n_events, 8192), kChunkThreads, 0, st>>>(d);
     return cudaGetLastError();
 }
 

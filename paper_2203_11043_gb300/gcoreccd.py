@@ -54,6 +54,9 @@ class GcParams(ctypes.Structure):
         ("jchunk", ctypes.c_int32),
         ("pair_R", ctypes.c_int32),
         ("timing", ctypes.c_int32),
+        ("stored_charge", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("stored_z_um", ctypes.c_double),
     ]
 
 

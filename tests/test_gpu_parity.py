@@ -422,3 +422,41 @@ def test_restore_rejects_inconsistent_state(gc):
             s.restore_state(bad)
         s.restore_state(st)  # the consistent one is accepted
         assert s.run(-1)[0] == gc.GC_OK
+
+
+# ---- stored charge (Sec. 1) ------------------------------------------------------------------
+
+def test_stored_charge_fp64_matches_oracle(gc):
+    """With the field of the charge already stored in the pixels on, the FP64
+    form reproduces the oracle: counts, collection steps and images exactly,
+    positions within 1e-4 um."""
+    wl = I.single_cloud(n=400, sigma_um=0.4, z0_um=35.0, seed=31, img=16)
+    kw = dict(pixel_um=3.0, stored_charge=1, stored_z_um=-0.2)
+    org = np.array([[-24.0, -24.0]])
+    wl = I.Workload(wl.name, wl.xyz, wl.ev_off, wl.seeds, org, 16, 16)
+    res = run_gpu(gc, wl, 0, **kw)
+    ref = run_oracle(wl, **kw)
+    assert_fp64_parity(res, ref, wl)
+    # the stored charge changes the result (it is not a no-op)
+    plain = run_oracle(wl, pixel_um=3.0)
+    assert not np.array_equal(plain.positions(), ref.positions())
+
+
+def test_stored_charge_ragged_batch_fp64(gc):
+    wl = ragged_batch()
+    kw = dict(pixel_um=1.0, stored_charge=1, stored_z_um=0.0)
+    res = run_gpu(gc, wl, 0, **kw)
+    ref = run_oracle(wl, **kw)
+    assert_fp64_parity(res, ref, wl)
+
+
+def test_stored_charge_fp32_statistics(gc):
+    wl = I.xray_5p9kev()
+    kw = dict(stored_charge=1, stored_z_um=0.0)
+    res = run_gpu(gc, wl, 2, **kw)
+    ref = run_oracle(wl, **kw)
+    assert res["n_collected"][0] == wl.n
+    for c in (0, 1):
+        assert res["positions"][:, c].std() == pytest.approx(ref.positions()[:, c].std(), rel=5e-3)
+    l1 = np.abs(res["image"].astype(np.int64) - ref.image.astype(np.int64)).sum()
+    assert l1 <= 0.01 * wl.n
