@@ -578,6 +578,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         occ_off[ie + 1] = occ_off[ie] + (int)std::min<long long>((long long)s->p.img_w * s->p.img_h, sizes[ie]);
     if (s->phys.stored) {
         GC_ALLOC(d.occ_pix, (size_t)std::max(occ_off[E], 1) * 4)
+        GC_ALLOC(d.occ_f4, (size_t)std::max(occ_off[E], 1) * 16)
         GC_ALLOC(d.occ_off, (E + 1) * 4) GC_ALLOC(d.occ_cnt, E * 4)
     }
     GC_ALLOC(d.keepmask, nchunk * (kChunk / 32) * 4) GC_ALLOC(d.chunk_cnt, nchunk * 4)

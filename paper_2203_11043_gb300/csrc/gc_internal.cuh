@@ -91,6 +91,7 @@ struct Dev {
     int *occ_pix;            // stored charge: occupied pixel indices, per event in index order
     int *occ_off;            // [E+1] capacity offsets of each event's occupied-pixel list
     int *occ_cnt;            // [E] occupied pixels this step
+    float4 *occ_f4;          // stored charge, FP32 forms: (centre x, y relative to the event origin, count, 0)
     unsigned long long *off_image;
     Ctrl *ctrl;
     int n_total;

@@ -50,6 +50,36 @@ __device__ __forceinline__ void normals32(uint4 b, float n[3]) {
     n[2] = r1 * cospif(2.0f * ((float)b.w * s));
 }
 
+// ---- block-wide exclusive scan (1024 threads) ------------------------------------------------
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *s_warp,
+                                                          long long &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = s_warp[lane];
+        long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        s_warp[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const long long ex = s_warp[warp] + incl - v;
+    total = s_warp[32];
+    __syncthreads();
+    return ex;
+}
+
 // ---- stored charge (Sec. 1) ----------------------------------------------------------
 // Field of the charge stored in event e's pixels at the carrier whose shadow
 // position (relative to the event origin o) is r: pixel (ix, iy) with count q
@@ -69,53 +99,80 @@ __device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, 
     const int *occ = d.occ_pix + d.occ_off[e];
     const int cnt = d.occ_cnt[e];
     sx = sy = sz = (T)0;
-    for (int k = 0; k < cnt; ++k) {
-        const int pidx = occ[k];
-        const int iy = pidx / ph.img_w, ix = pidx - iy * ph.img_w;
-        const T q = (T)img[pidx];
-        const T dx = rx0 - (cx0 + (T)ix * pix), dy = ry0 - (cy0 + (T)iy * pix);
-        const T r2 = dx * dx + dy * dy + dz * dz + eps2;
-        const T w = q / (r2 * sqrt(r2));
-        sx += dx * w;
-        sy += dy * w;
-        sz += dz * w;
+    if constexpr (sizeof(T) == 4) {  // FP32 forms: precomputed centres, MUFU rsqrt
+        const float4 *c4 = d.occ_f4 + d.occ_off[e];
+        for (int k = 0; k < cnt; ++k) {
+            const float4 cq = c4[k];
+            const float dx = rx0 - cq.x, dy = ry0 - cq.y;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            const float iv = rsqrt_mufu(r2);
+            const float w = cq.z * iv * iv * iv;
+            sx = fmaf(dx, w, sx);
+            sy = fmaf(dy, w, sy);
+            sz = fmaf(dz, w, sz);
+        }
+        (void)occ;
+        (void)img;
+        (void)cx0;
+        (void)cy0;
+        (void)pix;
+    } else {
+        for (int k = 0; k < cnt; ++k) {
+            const int pidx = occ[k];
+            const int iy = pidx / ph.img_w, ix = pidx - iy * ph.img_w;
+            const T q = (T)img[pidx];
+            const T dx = rx0 - (cx0 + (T)ix * pix), dy = ry0 - (cy0 + (T)iy * pix);
+            const T r2 = dx * dx + dy * dy + dz * dz + eps2;
+            const T w = q / (r2 * sqrt(r2));
+            sx += dx * w;
+            sy += dy * w;
+            sz += dz * w;
+        }
     }
 }
 
-// One block per event: the occupied pixels of its image in index order
-// (warp ballot + block prefix), for the stored-charge field of this step.
+// One block per event: the occupied pixels of its image in index order, for
+// the stored-charge field of this step.  Each thread takes 8 consecutive
+// pixels of a 8192-pixel span; one block-wide exclusive scan of the per-thread
+// counts places them.
+constexpr int kOccPer = 8;
 __global__ void __launch_bounds__(kChunkThreads) occupied_pixels_kernel(Dev d) {
-    __shared__ int s_warp[kChunkThreads / 32];
-    __shared__ int s_base;
+    __shared__ long long s_warp[33];
     Ctrl *c = d.ctrl;
     if (step_skipped(c)) return;
     const int npix = d.phys.img_w * d.phys.img_h;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int SPAN = kOccPer * kChunkThreads;
     for (int e = blockIdx.x; e < d.n_events; e += gridDim.x) {
         const unsigned *img = d.image + (long long)d.ev_user[e] * npix;
         int *out = d.occ_pix + d.occ_off[e];
         const int cap = d.occ_off[e + 1] - d.occ_off[e];
-        if (threadIdx.x == 0) s_base = 0;
-        __syncthreads();
-        for (int b0 = 0; b0 < npix; b0 += kChunkThreads) {
-            const int pidx = b0 + threadIdx.x;
-            const bool occ = pidx < npix && img[pidx] != 0u;
-            const unsigned m = __ballot_sync(0xffffffffu, occ);
-            if (lane == 0) s_warp[warp] = __popc(m);
-            __syncthreads();
-            int before = s_base;
-            for (int w = 0; w < warp; ++w) before += s_warp[w];
-            const int k = before + __popc(m & ((1u << lane) - 1u));
-            if (occ && k < cap) out[k] = pidx;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int t = 0;
-                for (int w = 0; w < kChunkThreads / 32; ++w) t += s_warp[w];
-                s_base += t;
-            }
-            __syncthreads();
+        long long base = 0;
+        for (int b0 = 0; b0 < npix; b0 += SPAN) {
+            const int first = b0 + threadIdx.x * kOccPer;
+            unsigned bits = 0u;
+#pragma unroll
+            for (int k = 0; k < kOccPer; ++k)
+                if (first + k < npix && img[first + k] != 0u) bits |= 1u << k;
+            long long total;
+            const long long ex = block_exclusive_scan((long long)__popc(bits), s_warp, total);
+            long long k_out = base + ex;
+#pragma unroll
+            for (int k = 0; k < kOccPer; ++k)
+                if ((bits >> k) & 1u) {
+                    if (k_out < cap) {
+                        const int pidx = first + k;
+                        out[k_out] = pidx;
+                        const int iy = pidx / d.phys.img_w, ix = pidx - iy * d.phys.img_w;
+                        d.occ_f4[d.occ_off[e] + k_out] = make_float4(
+                            (float)(d.img_origin[2 * e] + (ix + 0.5) * d.phys.pixel - d.ev_origin[3 * e]),
+                            (float)(d.img_origin[2 * e + 1] + (iy + 0.5) * d.phys.pixel - d.ev_origin[3 * e + 1]),
+                            (float)img[pidx], 0.0f);
+                    }
+                    ++k_out;
+                }
+            base += total;
         }
-        if (threadIdx.x == 0) d.occ_cnt[e] = min(s_base, cap);
+        if (threadIdx.x == 0) d.occ_cnt[e] = (int)(base < cap ? base : (long long)cap);
         __syncthreads();
     }
 }
@@ -353,36 +410,6 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
         }
         __syncthreads();
     }
-}
-
-// ---- block-wide exclusive scan (1024 threads) ------------------------------------------------
-__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *s_warp,
-                                                          long long &total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        long long w = s_warp[lane];
-        long long wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
-        }
-        s_warp[lane] = wi - w;  // exclusive prefix of warp totals
-        if (lane == 31) s_warp[32] = wi;
-    }
-    __syncthreads();
-    const long long ex = s_warp[warp] + incl - v;
-    total = s_warp[32];
-    __syncthreads();
-    return ex;
 }
 
 __device__ __forceinline__ int items_for(const Dev &d, int n) {
