@@ -251,7 +251,8 @@ def to_completion(args):
 
     def timed_run(w):
         p = gc.gc_default_params(precision=prec, img_w=w.img_w, img_h=w.img_h, pair_R=args.pair_R,
-                                 coulomb=args.coulomb, stored_charge=args.stored_charge)
+                                 coulomb=args.coulomb, stored_charge=args.stored_charge,
+                                 tile_frames=args.tile_frames)
         with gc.Simulation(p, w.xyz, w.ev_off, w.seeds, w.img_origin, stream=stream.cuda_stream) as s:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -268,6 +269,7 @@ def to_completion(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "mode": "to completion", "coulomb": args.coulomb,
             "stored_charge": args.stored_charge,
+            "tile_frames": args.tile_frames,
             "config": {"workload": WORKLOADS[args.workload], "n_carriers": wl.n,
                        "events": wl.n_events, "pair_R": stats["pair_variant"],
                        "jchunk": stats["jchunk"], "pair_blocks": stats["pair_blocks"]},
@@ -305,6 +307,8 @@ def main():
     ap.add_argument("--n-carriers", type=int, default=0,
                     help="run on a random sub-sample of the bundle (profiling small cases)")
     ap.add_argument("--pair-R", type=int, default=0, help="force the pair-kernel register blocking")
+    ap.add_argument("--tile-frames", type=int, default=0, choices=[0, 1],
+                    help="FP32 shadow relative to 256-slot tile origins for events of >= 8192 holes")
     ap.add_argument("--workload", default="bundle", choices=sorted(WORKLOADS))
     ap.add_argument("--to-completion", action="store_true",
                     help="time one run until every hole is collected (graphs, no per-step flush)")
@@ -342,7 +346,8 @@ def main():
     # single event is not sharded); seeds differ per rank
     seeds = replica_seeds(wl.seeds, rank)
     params = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
-                                  graph_steps=1, timing=1, pair_R=args.pair_R, coulomb=args.coulomb)
+                                  graph_steps=1, timing=1, pair_R=args.pair_R, coulomb=args.coulomb,
+                                  tile_frames=args.tile_frames)
     sim = gc.Simulation(params, wl.xyz, wl.ev_off, seeds, wl.img_origin, stream=stream.cuda_stream)
     st0 = sim.stats()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -400,6 +405,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "n_carriers": wl.n, "events": wl.n_events,
                        "precision": "FP32 pair sum with Kahan across j-tiles; FP64 positions",
+                       "frames": "tile (256-slot FP64 origins, Morton order)" if args.tile_frames
+                                 else "event centroid",
                        "pair_R": after["pair_variant"], "pair_blocks": after["pair_blocks"],
                        "jchunk": after["jchunk"], "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}", "device": f"sm_{ccmaj}{ccmin}, {sms} SMs"},
@@ -446,7 +453,8 @@ def main():
         e2e_steps = min(args.steps, 20)
         p = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
                                  graph_steps=min(32, e2e_steps), autotune=0,
-                                 pair_R=after["pair_variant"], jchunk=after["jchunk"])
+                                 pair_R=after["pair_variant"], jchunk=after["jchunk"],
+                                 tile_frames=args.tile_frames)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with gc.Simulation(p, wl.xyz, wl.ev_off, seeds, wl.img_origin, stream=stream.cuda_stream) as s3:

@@ -65,7 +65,7 @@ gc_status validate(const gc_params *p) {
     if (p->graph_steps < 0 || p->graph_steps > 4096) return GC_ERR_PARAM;
     if (p->jchunk < 0) return GC_ERR_PARAM;
     if ((p->coulomb | p->diffusion | p->reflect_back | p->autotune | p->newton | p->timing |
-         p->stored_charge) & ~1)
+         p->stored_charge | p->tile_frames) & ~1)
         return GC_ERR_PARAM;
     if (p->pair_R != 0 && p->pair_R != 2 && p->pair_R != 4 && p->pair_R != 8) return GC_ERR_PARAM;
     return GC_OK;
@@ -114,6 +114,44 @@ struct DevAllocs {
 
 int round_up(long long v, int m) { return (int)((v + m - 1) / m * m); }
 
+// Spread the low 21 bits of v so that bit k lands on bit 3k (for a 3-D
+// Morton / Z-order key): each step doubles the gap between bit groups.
+uint64_t spread_bits3(uint64_t v) {
+    v &= 0x1FFFFFull;
+    v = (v | (v << 32)) & 0x001F00000000FFFFull;
+    v = (v | (v << 16)) & 0x001F0000FF0000FFull;
+    v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+    v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+// Reorder ids[0..n) (one event) by the Morton key of their positions on a
+// 2^21 grid over the event's bounding box (ties by id), so that consecutive
+// slots are spatial neighbours.
+void morton_order(const double *xyz, int *ids, int n) {
+    if (n < 2) return;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int k = 0; k < n; ++k)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = std::min(lo[c], xyz[3LL * ids[k] + c]);
+            hi[c] = std::max(hi[c], xyz[3LL * ids[k] + c]);
+        }
+    const double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-30});
+    const double scale = 2097151.0 / ext;
+    std::vector<std::pair<uint64_t, int>> key(n);
+    for (int k = 0; k < n; ++k) {
+        uint64_t m = 0;
+        for (int c = 0; c < 3; ++c) {
+            const double q = std::min(2097151.0, std::max(0.0, (xyz[3LL * ids[k] + c] - lo[c]) * scale));
+            m |= spread_bits3((uint64_t)q) << c;
+        }
+        key[k] = {m, ids[k]};
+    }
+    std::sort(key.begin(), key.end());
+    for (int k = 0; k < n; ++k) ids[k] = key[k].second;
+}
+
 // j-chunk length: one chunk per event when the i-tiles alone give every
 // resident block >= 32 items; otherwise split j so that they do (at most 32
 // chunks), keeping dynamic-scheduling tail loss near 1/64 of a step.
@@ -152,6 +190,8 @@ struct gc_sim {
     int launches_per_step = 0;
     long long part_cap_chunks = 1;   // j-chunks the partial buffer can hold
     // timing: before the pair kernel, after it, after integrate, after compact
+    std::vector<int> load_act;       // the active list at load (event order, in-event order)
+    std::vector<int> load_off;       // its event offsets
     std::vector<cudaEvent_t> ev_a, ev_b, ev_c, ev_d;
     double pair_ms = 0.0, integ_ms = 0.0, compact_ms = 0.0;
     long long pair_launches = 0, timed_steps = 0;
@@ -193,6 +233,7 @@ gc_status enqueue_step(gc_sim *s, int k) {
     GC_CUDA(launch_compact(s->dev, f64, s->integ_grid, s->stream));
     if (timed) GC_CUDA(cudaEventRecord(s->ev_d[k], s->stream));
     GC_CUDA(launch_finalize(s->dev, false, s->stream));
+    if (s->dev.tile_frames) GC_CUDA(launch_shadow(s->dev, s->stream));
     return GC_OK;
 }
 
@@ -287,7 +328,7 @@ gc_status capture_graph(gc_sim *s) {
 gc_status choose_shape(gc_sim *s, const std::vector<long long> &sizes) {
     PairShape best = s->dev.shape;
     if (fp64_mode(s)) {
-        const int occ = std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0));
+        const int occ = std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0, 0));
         best.R = 1;
         best.small_n = 0;
         best.n_blocks = s->sm_count * occ;
@@ -310,8 +351,9 @@ gc_status choose_shape(gc_sim *s, const std::vector<long long> &sizes) {
     for (int ci = first; ci <= last; ++ci) {
         PairShape sh;
         sh.R = cands[ci];
-        sh.small_n = 8192;
-        const int occ = std::max(1, pair_kernel_occupancy(s->p.precision, sh.R, s->p.newton));
+        sh.small_n = kSmallEvent;
+        const int occ =
+            std::max(1, pair_kernel_occupancy(s->p.precision, sh.R, s->p.newton, s->dev.tile_frames));
         sh.n_blocks = s->sm_count * occ;
         sh.jchunk = choose_jchunk(sizes, sh.R, sh.small_n, sh.n_blocks, s->p.jchunk);
         long long n_max = 1;
@@ -526,6 +568,18 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         }
     }
     ioff[E] = pos;
+    // tile frames (FP32 forms, on request, when some event has >= small_n
+    // holes): the large events in spatial (Morton) order
+    const int small_n = kSmallEvent;
+    long long n_max = 1;
+    for (long long v : sizes) n_max = std::max(n_max, v);
+    const bool frames = s->p.tile_frames && !fp64_mode(s) && (s->phys.coulomb || s->phys.stored) &&
+                        n_max >= small_n;
+    if (frames)
+        for (int64_t ie = 0; ie < E; ++ie)
+            if (sizes[ie] >= small_n) morton_order(xyz, act.data() + ioff[ie], (int)sizes[ie]);
+    s->load_act.assign(act.begin(), act.begin() + pos);
+    s->load_off.assign(ioff.begin(), ioff.end());
     std::vector<int> ev_user(order.begin(), order.end()), ev_first(E);
     for (int64_t ie = 0; ie < E; ++ie) ev_first[ie] = (int)uoff[order[ie]];
     std::vector<double> hx(std::max<int64_t>(n, 1)), hy(hx.size()), hz(hx.size());
@@ -536,13 +590,11 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     }
 
     // partial-sum capacity: enough j-chunks for every autotune candidate
-    long long n_max = 1;
-    for (long long v : sizes) n_max = std::max(n_max, v);
     long long cap = 1;
     if (!fp64_mode(s) && s->phys.coulomb) {
         for (int R : {2, 4, 8}) {
-            const int occ = std::max(1, pair_kernel_occupancy(s->p.precision, R, s->p.newton));
-            const int jc = choose_jchunk(sizes, R, 8192, s->sm_count * occ, s->p.jchunk);
+            const int occ = std::max(1, pair_kernel_occupancy(s->p.precision, R, s->p.newton, frames));
+            const int jc = choose_jchunk(sizes, R, kSmallEvent, s->sm_count * occ, s->p.jchunk);
             cap = std::max(cap, (n_max + jc - 1) / jc);
         }
     }
@@ -573,6 +625,9 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     if (s->p.precision == GC_FP16X2) {
         GC_ALLOC(d.ev_ext[0], E * 4) GC_ALLOC(d.ev_ext[1], E * 4)
     }
+    if (frames) {
+        GC_ALLOC(d.frame_hi, N * sizeof(float4)) GC_ALLOC(d.frame_lo, N * sizeof(float4))
+    }
     std::vector<int> occ_off(E + 1, 0);  // stored charge: per-event occupied-pixel capacity
     for (int64_t ie = 0; ie < E; ++ie)
         occ_off[ie + 1] = occ_off[ie] + (int)std::min<long long>((long long)s->p.img_w * s->p.img_h, sizes[ie]);
@@ -594,7 +649,8 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     d.n_events = (int)E;
     d.phys = s->phys;
     d.shape.R = fp64_mode(s) ? 1 : 4;
-    d.shape.small_n = fp64_mode(s) ? 0 : 8192;
+    d.shape.small_n = fp64_mode(s) ? 0 : small_n;
+    d.tile_frames = frames ? 1 : 0;
     d.shape.jchunk = round_up(n_max, kTileJ);
     d.shape.n_blocks = s->sm_count;
 
@@ -634,6 +690,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         GC_CUDA(launch_integrate(d, f64, true, s->integ_grid, st));
         GC_CUDA(launch_compact(d, f64, s->integ_grid, st));
         GC_CUDA(launch_finalize(d, true, st));
+        if (d.tile_frames) GC_CUDA(launch_shadow(d, st));
     }
     GC_CUDA(cudaStreamSynchronize(st));
     gc_status r = read_ctrl(s);
@@ -646,7 +703,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     if (r != GC_OK) return r;
     r = read_ctrl(s);
     if (r != GC_OK) return r;
-    s->launches_per_step = (s->phys.coulomb ? 1 : 0) + (s->phys.stored ? 1 : 0) + 3;
+    s->launches_per_step = (s->phys.coulomb ? 1 : 0) + (s->phys.stored ? 1 : 0) + (frames ? 1 : 0) + 3;
     if (s->p.timing) {
         for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
             v->resize(1);
@@ -862,15 +919,13 @@ gc_status gc_restore_state(gc_sim *s, const gc_state *st) {
     GC_CUDA(cudaSetDevice(s->device));
     Dev &d = s->dev;
     cudaStream_t q = s->stream;
-    // the active list in the load order: internal events, ascending id within each
-    std::vector<int> ev_user(E), act(std::max<int64_t>(n, 1)), ioff(E + 1);
-    GC_CUDA(cudaMemcpy(ev_user.data(), d.ev_user, E * 4, cudaMemcpyDeviceToHost));
+    // the active list in the load order (what stable compaction has kept)
+    std::vector<int> act(std::max<int64_t>(n, 1)), ioff(E + 1);
     int pos = 0;
     for (int64_t ie = 0; ie < E; ++ie) {
         ioff[ie] = pos;
-        const int ue = ev_user[ie];
-        for (int64_t id = s->user_off[ue]; id < s->user_off[ue + 1]; ++id)
-            if (st->collect_step[id] < 0) act[pos++] = (int)id;
+        for (int k = s->load_off[ie]; k < s->load_off[ie + 1]; ++k)
+            if (st->collect_step[s->load_act[k]] < 0) act[pos++] = s->load_act[k];
     }
     ioff[E] = pos;
     std::vector<double> hx(std::max<int64_t>(n, 1)), hy(hx.size()), hz(hx.size());
@@ -908,6 +963,7 @@ gc_status gc_restore_state(gc_sim *s, const gc_state *st) {
         GC_CUDA(launch_integrate(d, f64, true, s->integ_grid, q));
         GC_CUDA(launch_compact(d, f64, s->integ_grid, q));
         GC_CUDA(launch_finalize(d, true, q));
+        if (d.tile_frames) GC_CUDA(launch_shadow(d, q));
     }
     gc_status r = set_limit(s, st->step);
     if (r != GC_OK) return r;
@@ -943,13 +999,13 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
     if (f64) {
         d.shape.R = 1;
         d.shape.small_n = 0;
-        d.shape.n_blocks = sms * std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0));
+        d.shape.n_blocks = sms * std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0, 0));
         d.shape.jchunk = round_up(n, kTileJ);
     } else {
         d.shape.R = 4;
-        d.shape.small_n = 8192;
-        d.shape.n_blocks = sms * std::max(1, pair_kernel_occupancy(precision, 4, 0));
-        d.shape.jchunk = choose_jchunk(sizes, 4, 8192, d.shape.n_blocks, 0);
+        d.shape.small_n = kSmallEvent;
+        d.shape.n_blocks = sms * std::max(1, pair_kernel_occupancy(precision, 4, 0, 0));
+        d.shape.jchunk = choose_jchunk(sizes, 4, kSmallEvent, d.shape.n_blocks, 0);
     }
     const long long S = (n + d.shape.jchunk - 1) / d.shape.jchunk;
     DevAllocs m;

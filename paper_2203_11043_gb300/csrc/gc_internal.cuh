@@ -4,10 +4,17 @@
 // Data layout in HBM (N = carriers loaded, E = events, S = j-chunks):
 //   per carrier, by original id:  px, py, pz (FP64 SoA), ev_of_id (int32),
 //                                 collect_step (int32, -1 while active)
-//   per active slot (compacted, grouped by event, ascending id inside an
-//   event):                       act[cur] (id), sh32 (float4 shadow x,y,z
-//                                 relative to the event origin) or sh64
-//                                 (double4_32a, FP64 form), partial (FP64,
+//   per active slot (compacted, grouped by event; inside an event ascending
+//   id, or load-time Morton order for large events with tile frames):
+//                                 act[cur] (id), sh32 (float4 shadow x,y,z
+//                                 relative to its frame: the event centroid,
+//                                 or with tile frames, for events of >=
+//                                 small_n holes, the first hole of its
+//                                 256-slot tile counted from the event
+//                                 start) or sh64 (double4_32a, FP64 form,
+//                                 event frame), frame_hi/frame_lo (tile
+//                                 frames: the FP64 origin at each tile start
+//                                 as an FP32 hi + lo pair), partial (FP64,
 //                                 [S][3][N]), keepmask (1 bit per slot)
 //   per event (internal order = descending initial size):
 //                                 ev_off[cur] (active offsets), item_base
@@ -24,6 +31,9 @@ constexpr int kChunkThreads = 1024; // threads per integrate/compact block
 constexpr int kPairThreads = 128;   // threads per pair-kernel block
 constexpr int kTileJ = 256;         // j positions staged in shared memory per tile
 constexpr float kSentinel = 1.0e15f; // padding position: its Eq. 6 term rounds to 0
+constexpr int kSmallEvent = 8192;    // FP32 forms: smaller events split j over 4 lanes and use
+                                     // the event frame; larger ones one lane (and, with
+                                     // tile_frames, tile frames)
 
 // Control block: one per simulation, written only by the device during a run.
 struct Ctrl {
@@ -74,6 +84,9 @@ struct Dev {
     int *act[2];
     float4 *sh32;
     double4_32a *sh64;
+    float4 *frame_hi;        // FP32 forms, large events: frame origin at each tile-start slot,
+    float4 *frame_lo;        //   as float(o) and float(o - float(o))
+    int tile_frames;         // 1: large events use 256-slot tile frames (FP32 forms)
     double *partial;
     long long part_stride;
     unsigned *keepmask;
@@ -198,5 +211,13 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+
+// 16-byte asynchronous global -> shared copy (no register staging); both
+// addresses 16-byte aligned.  cp_async_wait_all() waits for this thread's copies.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 }  // namespace gc

@@ -6,9 +6,10 @@
 
 namespace gc {
 
-// Pair kernel (Eq. 6): precision 0 = FP64 form, 1 = FP32, 2 = FP32 + Kahan.
-const void *pair_kernel_ptr(int precision, int R, int newton);
-int pair_kernel_occupancy(int precision, int R, int newton);
+// Pair kernel (Eq. 6): precision 0 = FP64 form, 1 = FP32, 2 = FP32 + Kahan,
+// 3 = FP16x2; tile_frames != 0 selects the FP32 forms' tile-frame variant.
+const void *pair_kernel_ptr(int precision, int R, int newton, int tile_frames);
+int pair_kernel_occupancy(int precision, int R, int newton, int tile_frames);
 cudaError_t launch_pair(const Dev &d, int precision, int newton, cudaStream_t st);
 
 // One time step after the pair sum: integrate (mobility, drift, diffusion,
@@ -17,6 +18,10 @@ cudaError_t launch_pair(const Dev &d, int precision, int newton, cudaStream_t st
 cudaError_t launch_integrate(const Dev &d, bool fp64, bool init, int grid, cudaStream_t st);
 cudaError_t launch_compact(const Dev &d, bool fp64, int grid, cudaStream_t st);
 cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st);
+// FP32 forms with tile frames: the position shadow for the next step (tile
+// frames for large events, the event centroid otherwise) and the FP16x2
+// extents.  Without tile frames the compaction writes the shadow.
+cudaError_t launch_shadow(const Dev &d, cudaStream_t st);
 // Stored charge (Sec. 1): the occupied pixels of each event's image, in
 // pixel-index order, as the field sources of the coming integrate.
 cudaError_t launch_occupied_pixels(const Dev &d, cudaStream_t st);

@@ -104,9 +104,9 @@ extern "C" gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, 
     const bool f64 = precision == GC_FP64;
     const int R = f64 ? 1 : 4;
     d.shape.R = R;
-    d.shape.small_n = f64 ? 0 : 8192;
-    d.shape.n_blocks = sms * (pair_kernel_occupancy(precision, R, 0) > 0
-                                  ? pair_kernel_occupancy(precision, R, 0) : 1);
+    d.shape.small_n = f64 ? 0 : kSmallEvent;
+    d.shape.n_blocks = sms * (pair_kernel_occupancy(precision, R, 0, 0) > 0
+                                  ? pair_kernel_occupancy(precision, R, 0, 0) : 1);
     // at most kMaxChunks j-chunks, each a multiple of the shared-memory tile
     const long long per = f64 ? n : (n + kMaxChunks - 1) / kMaxChunks;
     d.shape.jchunk = (int)((per + kTileJ - 1) / kTileJ * kTileJ);

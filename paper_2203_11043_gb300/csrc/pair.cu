@@ -40,10 +40,22 @@ namespace gc {
 // power-of-two scale s (exact), the differences are rounded to f16x2 and
 // r^2 s^2 is formed with packed half FMAs; the reciprocal square root and the
 // accumulation stay FP32 and the sum is multiplied by s^2 at the end.
-template <int R, bool KAHAN, bool NEWTON, int L, bool H16>
+//
+// Tile frames (TF; large events, one lane per i-group): the shadow of a hole
+// is relative to the FP64 origin of its 256-slot tile, held as an FP32 hi + lo
+// pair.  An item works in the frame I of its first i-tile: each i and, while
+// a j-tile is staged, each j is moved into I by adding (hi_t - hi_I) +
+// (lo_t - lo_I) for its own tile t.  The i's are shifted once per item (they
+// stay loop-invariant, as in the event frame), both sides use the same
+// expression, so a hole's self term stays exactly 0, and differences of close
+// holes are taken between small FP32 numbers.  The j-tile origins reach
+// shared memory (s_fr) by cp.async with the tile before.  s_fr is written by
+// other threads, so it is not a restrict pointer.
+template <int R, bool KAHAN, bool NEWTON, int L, bool H16, bool TF>
 __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int n_e, int local,
                                                  float scale, float *__restrict__ sx,
-                                                 float *__restrict__ sy, float *__restrict__ sz) {
+                                                 float *__restrict__ sy, float *__restrict__ sz,
+                                                 float4 *s_fr) {
     constexpr int G = 32 / L;
     constexpr int STRIDE = kPairThreads / L;
     constexpr int IB = R * STRIDE;
@@ -61,11 +73,26 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
     f2 xi[R], yi[R], zi[R], ax[R], ay[R], az[R];
     const f2 ZERO = pack2(0.f, 0.f);
     f2 kreg[KAHAN ? 6 * R : 1];  // Kahan sums and compensations, {even, odd} j
+    float4 Ih = make_float4(0.f, 0.f, 0.f, 0.f), Il = Ih;  // tile frames: the item frame I
+    if (TF) {
+        Ih = d.frame_hi[e_start + it * IB];  // it * IB is a tile start
+        Il = d.frame_lo[e_start + it * IB];
+        if (tid < 2) s_fr[tid] = tid ? Il : Ih;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         float4 a = make_float4(kSentinel, kSentinel, kSentinel, 0.f);
         const int ia = il0 + r * STRIDE;
-        if (ia < n_e) a = d.sh32[e_start + ia];
+        if (ia < n_e) {
+            a = d.sh32[e_start + ia];
+            if (TF) {  // into the item frame
+                const int t = e_start + (ia & ~(kTileJ - 1));
+                const float4 th = d.frame_hi[t], tl = d.frame_lo[t];
+                a.x = a.x + ((th.x - Ih.x) + (tl.x - Il.x));
+                a.y = a.y + ((th.y - Ih.y) + (tl.y - Il.y));
+                a.z = a.z + ((th.z - Ih.z) + (tl.z - Il.z));
+            }
+        }
         if (H16) {
             a.x *= scale;
             a.y *= scale;
@@ -87,29 +114,48 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
     const int j0 = jc * jchunk;
     const int j1 = min(n_e, j0 + jchunk);
     float4 pre[PER];
+    float4 *s_fj = s_fr + 2;  // j-tile frames (hi, lo), double-buffered by tile parity
     auto fetch = [&](int jt) {
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int j = jt + u * kPairThreads + tid;
             pre[u] = j < j1 ? d.sh32[e_start + j] : make_float4(kSentinel, kSentinel, kSentinel, 0.f);
         }
+        if (TF && tid < 2)  // jt is a tile start (j-chunks are whole tiles)
+            cp_async16(s_fj + 2 * ((jt / TJ) & 1) + tid,
+                       (tid ? d.frame_lo : d.frame_hi) + e_start + jt);
     };
     fetch(j0);
     for (int jt = j0; jt < j1; jt += TJ) {
+        if (TF && tid < 2) cp_async_wait_all();  // this tile's frame has landed
         __syncthreads();  // the previous tile has been consumed
+        float ox = 0.f, oy = 0.f, oz = 0.f;
+        if (TF) {  // this j-tile's frame relative to the item frame
+            const int b = 2 * ((jt / TJ) & 1);
+            const float4 th = s_fj[b], tl = s_fj[b + 1], ih = s_fr[0], il = s_fr[1];
+            ox = (th.x - ih.x) + (tl.x - il.x);
+            oy = (th.y - ih.y) + (tl.y - il.y);
+            oz = (th.z - ih.z) + (tl.z - il.z);
+        }
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int k = u * kPairThreads + tid;
             const float sc = H16 ? scale : 1.0f;  // exact (power of two)
-            sx[k] = pre[u].x * sc;
-            sy[k] = pre[u].y * sc;
-            sz[k] = pre[u].z * sc;
+            if (TF) {
+                sx[k] = (pre[u].x + ox) * sc;
+                sy[k] = (pre[u].y + oy) * sc;
+                sz[k] = (pre[u].z + oz) * sc;
+            } else {
+                sx[k] = pre[u].x * sc;
+                sy[k] = pre[u].y * sc;
+                sz[k] = pre[u].z * sc;
+            }
         }
         __syncthreads();
         const int cnt = min(TJ, j1 - jt);
         if (jt + TJ < j1) fetch(jt + TJ);  // overlaps the loads with this tile's work
         const int kmax = (cnt + STEP - 1) / STEP * STEP;  // padded with sentinels
-        for (int k0 = 4 * ph; k0 < kmax; k0 += STEP) {
+        auto j_step = [&](const int k0) {  // 4 * JU j's per lane: two packed pairs per load
 #pragma unroll
             for (int u = 0; u < JU; ++u) {
                 const int k = k0 + u * 4 * L;
@@ -152,6 +198,12 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
                     }
                 }
             }
+        };
+        if (TF) {  // measured: unrolling by 2 suits the tile-frame variant, not the other
+#pragma unroll 2
+            for (int k0 = 4 * ph; k0 < kmax; k0 += STEP) j_step(k0);
+        } else {
+            for (int k0 = 4 * ph; k0 < kmax; k0 += STEP) j_step(k0);
         }
         if (KAHAN) {  // fold this tile's sums into the compensated totals
 #pragma unroll
@@ -214,9 +266,12 @@ __device__ __forceinline__ int event_of_item(const int *__restrict__ base, int n
 // Min blocks = 1 lets ptxas keep many independent pair chains in registers
 // (R = 4: ~246 registers, 2 blocks per SM); measured faster than letting it
 // trade registers for occupancy.
-template <int R, bool KAHAN, bool NEWTON, bool H16>
+// TF: the tile-frame variant (used when some event is large enough for one
+// lane per i-group); its small events still run the event-frame path.
+template <int R, bool KAHAN, bool NEWTON, bool H16, bool TF>
 __global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
     __shared__ __align__(16) float s_x[kTileJ], s_y[kTileJ], s_z[kTileJ];
+    __shared__ float4 s_fr[TF ? 6 : 1];  // tile frames: the item frame, then two j-tile frames
     __shared__ int s_item;
     Ctrl *c = d.ctrl;
     if (step_skipped(c)) return;
@@ -233,9 +288,11 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
         const int local = item - d.item_base[e];
         const float scale = H16 ? h2_scale(__uint_as_float(ext[e])) : 1.0f;
         if (lanes_for(n_e, d.shape.small_n) == 1)
-            pair_item_fp32_j<R, KAHAN, NEWTON, 1, H16>(d, e_start, n_e, local, scale, s_x, s_y, s_z);
+            pair_item_fp32_j<R, KAHAN, NEWTON, 1, H16, TF>(d, e_start, n_e, local, scale, s_x, s_y,
+                                                           s_z, s_fr);
         else
-            pair_item_fp32_j<R, KAHAN, NEWTON, 4, H16>(d, e_start, n_e, local, scale, s_x, s_y, s_z);
+            pair_item_fp32_j<R, KAHAN, NEWTON, 4, H16, false>(d, e_start, n_e, local, scale, s_x, s_y,
+                                                              s_z, s_fr);
         __syncthreads();  // s_item and the tiles are reused by the next item
     }
 }
@@ -301,14 +358,15 @@ __global__ void __launch_bounds__(kPairThreads) pair_fp64_kernel(Dev d) {
 // Host-side launch table.
 typedef void (*PairKernel)(Dev);
 
+template <bool TF>
 static PairKernel fp32_kernel(int R, bool kahan, bool newton, bool h16) {
 #define GC_PICK(RR)                                                                        \
     if (R == RR) {                                                                         \
-        if (h16) return pair_fp32_kernel<RR, true, false, true>; /* no Newton step */      \
-        if (kahan) return newton ? pair_fp32_kernel<RR, true, true, false>                 \
-                                 : pair_fp32_kernel<RR, true, false, false>;               \
-        return newton ? pair_fp32_kernel<RR, false, true, false>                           \
-                      : pair_fp32_kernel<RR, false, false, false>;                         \
+        if (h16) return pair_fp32_kernel<RR, true, false, true, TF>; /* no Newton step */  \
+        if (kahan) return newton ? pair_fp32_kernel<RR, true, true, false, TF>             \
+                                 : pair_fp32_kernel<RR, true, false, false, TF>;           \
+        return newton ? pair_fp32_kernel<RR, false, true, false, TF>                       \
+                      : pair_fp32_kernel<RR, false, false, false, TF>;                     \
     }
     GC_PICK(2)
     GC_PICK(4)
@@ -317,15 +375,18 @@ static PairKernel fp32_kernel(int R, bool kahan, bool newton, bool h16) {
     return nullptr;
 }
 
-const void *pair_kernel_ptr(int precision, int R, int newton) {
+const void *pair_kernel_ptr(int precision, int R, int newton, int tile_frames) {
     if (precision == 0) return (const void *)pair_fp64_kernel;
-    if (precision >= 1 && precision <= 3)
-        return (const void *)fp32_kernel(R, precision >= 2, newton != 0, precision == 3);
+    if (precision >= 1 && precision <= 3) {
+        const bool kahan = precision >= 2, h16 = precision == 3;
+        return tile_frames ? (const void *)fp32_kernel<true>(R, kahan, newton != 0, h16)
+                           : (const void *)fp32_kernel<false>(R, kahan, newton != 0, h16);
+    }
     return nullptr;
 }
 
-int pair_kernel_occupancy(int precision, int R, int newton) {
-    const void *k = pair_kernel_ptr(precision, R, newton);
+int pair_kernel_occupancy(int precision, int R, int newton, int tile_frames) {
+    const void *k = pair_kernel_ptr(precision, R, newton, tile_frames);
     if (!k) return 0;
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kPairThreads, 0) != cudaSuccess)
@@ -334,7 +395,7 @@ int pair_kernel_occupancy(int precision, int R, int newton) {
 }
 
 cudaError_t launch_pair(const Dev &d, int precision, int newton, cudaStream_t st) {
-    const void *k = pair_kernel_ptr(precision, d.shape.R, newton);
+    const void *k = pair_kernel_ptr(precision, d.shape.R, newton, d.tile_frames);
     if (!k) return cudaErrorInvalidValue;
     ((PairKernel)k)<<<d.shape.n_blocks, kPairThreads, 0, st>>>(d);
     return cudaGetLastError();

@@ -50,6 +50,71 @@ __device__ __forceinline__ void normals32(uint4 b, float n[3]) {
     n[2] = r1 * cospif(2.0f * ((float)b.w * s));
 }
 
+// ---- FP32 position shadow with tile frames -------------------------------------------------------
+// Runs after finalize when tile frames are on (the new active list and event
+// offsets are current; without tile frames the compaction writes the shadow).
+// Events with at least small_n active holes (the ones whose pair items run
+// one lane per i-group) get tile frames: slot q of event e (start e0) is
+// stored relative to the FP64 position of the hole in slot
+// e0 + ((q - e0) rounded down to 256), so the FP32 coordinates of spatially
+// close holes (load-time Morton order) stay small; that origin is stored at
+// the tile start as an FP32 hi + lo pair.  Smaller events use the event
+// centroid.  It also measures the FP16x2 extents (max |r - centroid|).
+// Rebuilding from the current state is idempotent, so it needs no skip flag.
+__global__ void __launch_bounds__(256) shadow_kernel(Dev d) {
+    Ctrl *c = d.ctrl;
+    const int n = c->n_active;
+    if (n <= 0) return;
+    const int cur = c->cur;
+    const int *act = d.act[cur];
+    const int *off = d.ev_off[cur];
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    const int n_round = (n + 31) / 32 * 32;  // whole warps stay in the loop
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_round; q += stride) {
+        const bool valid = q < n;
+        int e = -1;
+        unsigned ext_bits = 0u;
+        if (valid) {
+            const int id = act[q];
+            e = d.ev_of_id[id];
+            const int e0 = off[e], ne = off[e + 1] - e0;
+            const double x = d.px[id], y = d.py[id], z = d.pz[id];
+            const double cx = d.ev_origin[3 * e], cy = d.ev_origin[3 * e + 1], cz = d.ev_origin[3 * e + 2];
+            double ox = cx, oy = cy, oz = cz;
+            if (d.tile_frames && ne >= d.shape.small_n) {
+                const int rs = e0 + ((q - e0) & ~(kTileJ - 1));
+                const int rid = act[rs];
+                ox = d.px[rid];
+                oy = d.py[rid];
+                oz = d.pz[rid];
+                if (q == rs) {
+                    const float hx = (float)ox, hy = (float)oy, hz = (float)oz;
+                    d.frame_hi[q] = make_float4(hx, hy, hz, 0.f);
+                    d.frame_lo[q] = make_float4((float)(ox - hx), (float)(oy - hy), (float)(oz - hz), 0.f);
+                }
+            }
+            d.sh32[q] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 1.0f);
+            if (d.ev_ext[0])
+                ext_bits = __float_as_uint(fmaxf(fabsf((float)(x - cx)),
+                                                 fmaxf(fabsf((float)(y - cy)), fabsf((float)(z - cz)))));
+        }
+        if (d.ev_ext[0]) {  // FP16x2 form: per-event max |r - centroid|, warp-aggregated
+            unsigned *ext = d.ev_ext[cur];
+            const unsigned lead = __ffs(__ballot_sync(0xffffffffu, valid));
+            if (lead) {
+                const int e0 = __shfl_sync(0xffffffffu, e, lead - 1);
+                if (__all_sync(0xffffffffu, !valid || e == e0)) {
+                    const unsigned mx = __reduce_max_sync(0xffffffffu, ext_bits);
+                    if (lane == 0) atomicMax(&ext[e0], mx);
+                } else if (valid) {
+                    atomicMax(&ext[e], ext_bits);
+                }
+            }
+        }
+    }
+}
+
 // ---- block-wide exclusive scan (1024 threads) ------------------------------------------------
 __device__ __forceinline__ long long block_exclusive_scan(long long v, long long *s_warp,
                                                           long long &total) {
@@ -215,10 +280,11 @@ __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long 
                 ex += ph.K * sx;
                 ey += ph.K * sy;
                 ez += ph.K * sz;
-            } else {
-                const float4 r = d.sh32[p];
+            } else {  // the FP32 shadow may be tile-relative: use the event frame here
+                const float rx = (float)(x - d.ev_origin[3 * e]), ry = (float)(y - d.ev_origin[3 * e + 1]),
+                            rz = (float)(z - d.ev_origin[3 * e + 2]);
                 float sx, sy, sz;
-                stored_field<float>(d, e, r.x, r.y, r.z, sx, sy, sz);
+                stored_field<float>(d, e, rx, ry, rz, sx, sy, sz);
                 ex += ph.K * (double)sx;
                 ey += ph.K * (double)sy;
                 ez += ph.K * (double)sz;
@@ -380,13 +446,15 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
                 const int q = base + s_wpre[m] + __popc(w & ((1u << lane) - 1u));
                 const int id = src[p];
                 dst[q] = id;
+                // the shadow in the event frame (with tile frames the FP32 shadow
+                // is written by shadow_kernel once the new event offsets are known)
                 if (d.phys.coulomb || d.phys.stored) {  // the O(N) path reads no shadow
                     e = d.ev_of_id[id];
                     const double ox = d.ev_origin[3 * e], oy = d.ev_origin[3 * e + 1],
                                  oz = d.ev_origin[3 * e + 2];
                     if (F64) {
                         d.sh64[q] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
-                    } else {
+                    } else if (!d.tile_frames) {
                         const float4 v = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
                                                      (float)(d.pz[id] - oz), 1.0f);
                         d.sh32[q] = v;
@@ -394,8 +462,8 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
                     }
                 }
             }
-            if (!F64 && d.ev_ext[0] && (d.phys.coulomb || d.phys.stored)) {  // FP16x2: max |coordinate|
-                unsigned *ext = d.ev_ext[cur ^ 1];
+            if (!F64 && !d.tile_frames && d.ev_ext[0] && (d.phys.coulomb || d.phys.stored)) {
+                unsigned *ext = d.ev_ext[cur ^ 1];  // FP16x2: max |coordinate|, warp-aggregated
                 const unsigned lead = __ffs(__ballot_sync(0xffffffffu, keep));
                 if (lead) {
                     const int e0 = __shfl_sync(0xffffffffu, e, lead - 1);
@@ -567,6 +635,12 @@ cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st) {
 
 cudaError_t launch_loop_cond(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st) {
     loop_cond_kernel<<<1, 32, 0, st>>>(d, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow(const Dev &d, cudaStream_t st) {
+    const int grid = max(1, min(ceil_div(d.n_total, 256), 8 * 152));
+    shadow_kernel<<<grid, 256, 0, st>>>(d);
     return cudaGetLastError();
 }
 

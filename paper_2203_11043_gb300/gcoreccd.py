@@ -55,7 +55,7 @@ class GcParams(ctypes.Structure):
         ("pair_R", ctypes.c_int32),
         ("timing", ctypes.c_int32),
         ("stored_charge", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tile_frames", ctypes.c_int32),
         ("stored_z_um", ctypes.c_double),
     ]
 

@@ -58,7 +58,7 @@ def test_param_struct_layout(lib):
     assert (p.img_w, p.img_h, p.pixel_um) == (64, 64, 15.0)
     assert (p.graph_steps, p.autotune, p.newton, p.jchunk, p.pair_R, p.timing) == (32, 1, 0, 0, 0, 0)
     assert p.precision == gc.GC_FP32_KAHAN
-    assert (p.stored_charge, p.stored_z_um) == (0, 0.0)
+    assert (p.stored_charge, p.stored_z_um, p.tile_frames) == (0, 0.0, 0)
 
 
 @pytest.mark.parametrize("field,value", [
@@ -66,7 +66,7 @@ def test_param_struct_layout(lib):
     ("T_K", -1.0), ("thickness_um", 0.0), ("z_well_um", 700.0), ("pixel_um", 0.0), ("img_w", 0),
     ("img_h", -3), ("max_steps", -1), ("softening_um", 0.0), ("eps_si_rel", 0.0),
     ("graph_steps", -1), ("jchunk", -5), ("coulomb", 2), ("pair_R", 3), ("timing", 2),
-    ("stored_charge", 2), ("stored_z_um", float("inf")),
+    ("stored_charge", 2), ("stored_z_um", float("inf")), ("tile_frames", 2), ("tile_frames", -1),
 ])
 def test_invalid_params_rejected_before_any_cuda_call(lib, field, value):
     import paper_2203_11043_gb300 as gc

@@ -337,6 +337,7 @@ def test_large_one_step_sampled(gc):
     tg = np.sort(rng.choice(active, size=48, replace=False))
     want = O.step_targets(O.make_params(img_w=512, img_h=512), x0, active, tg, int(wl.seeds[0]), 1)
     err = np.abs(x1[tg] - want).max()
+    print(f"one step at 1,048,576 holes, FP32 + Kahan vs oracle: max |dr| {err:.2e} um")
     assert err < 1e-4, err
 
 

@@ -144,17 +144,19 @@ def muon10k(gc):
     return wl, run(gc, wl, gc.GC_FP64)
 
 
-@pytest.mark.parametrize("precision", [2, 3])
-def test_muon_run_forms_against_fp64(gc, muon10k, precision):
+@pytest.mark.parametrize("precision,tile_frames", [(2, 0), (3, 0), (2, 1), (3, 1)])
+def test_muon_run_forms_against_fp64(gc, muon10k, precision, tile_frames):
     """Full runs of a 10,000-hole track (the 2.5 mm geometry at 1/20 of the
-    density): FP32 + Kahan and FP16x2 against the FP64 form on the GPU."""
+    density): FP32 + Kahan and FP16x2, in the event frame and in tile frames,
+    against the FP64 form on the GPU."""
     wl, ref = muon10k
-    got = run(gc, wl, precision)
+    got = run(gc, wl, precision, tile_frames=tile_frames)
     assert got["status"] == ref["status"] == gc.GC_OK
     assert got["n_collected"][0] == ref["n_collected"][0] == wl.n
     assert_statistics(got["positions"], ref["positions"], got["image"][0], ref["image"][0], wl.n)
     d = np.abs(got["positions"] - ref["positions"])[:, :2].max(axis=1)
-    print(f"precision {precision}: per-hole final |dxy| vs FP64: median {np.median(d):.2e} um, "
+    print(f"precision {precision}, tile frames {tile_frames}: per-hole final |dxy| vs FP64: "
+          f"median {np.median(d):.2e} um, "
           f"99th pct {np.percentile(d, 99):.2e} um, max {d.max():.2e} um")
 
 
