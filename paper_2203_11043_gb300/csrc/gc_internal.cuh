@@ -212,11 +212,17 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
     return r;
 }
 
-// 16-byte asynchronous global -> shared copy (no register staging); both
-// addresses 16-byte aligned.  cp_async_wait_all() waits for this thread's copies.
+// 16-byte asynchronous global -> shared copies (no register staging); both
+// addresses 16-byte aligned.  The _zfill form copies `bytes` (0 or 16) and
+// zero-fills the rest.  cp_async_wait_all() waits for this thread's copies.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, unsigned bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(bytes)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 

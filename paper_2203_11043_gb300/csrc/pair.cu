@@ -14,9 +14,9 @@
 //    packed FP32 pair {x_i, x_i}, and pairs it with two j's at a time: every
 //    step of the pair term runs as packed f32x2 instructions
 //    (sub/fma/mul .f32x2) with the reciprocal square root on MUFU;
-//  * j positions are staged in shared memory as SoA tiles, so one 16-byte
-//    broadcast load per coordinate feeds four j's (two packed pairs) to
-//    every i of the thread;
+//  * j positions arrive by cp.async one tile ahead and are staged in shared
+//    memory as SoA tiles, so one 16-byte broadcast load per coordinate feeds
+//    four j's (two packed pairs) to every i of the thread;
 //  * per-tile FP32 sums are folded into Kahan-compensated running sums
 //    (FP32_KAHAN), and each item writes an FP64 partial per j-chunk; the
 //    integrate kernel adds the chunks in a fixed order (deterministic);
@@ -55,7 +55,7 @@ template <int R, bool KAHAN, bool NEWTON, int L, bool H16, bool TF>
 __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int n_e, int local,
                                                  float scale, float *__restrict__ sx,
                                                  float *__restrict__ sy, float *__restrict__ sz,
-                                                 float4 *s_fr) {
+                                                 float4 *s_fr, float4 *s_raw) {
     constexpr int G = 32 / L;
     constexpr int STRIDE = kPairThreads / L;
     constexpr int IB = R * STRIDE;
@@ -113,13 +113,16 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
 
     const int j0 = jc * jchunk;
     const int j1 = min(n_e, j0 + jchunk);
-    float4 pre[PER];
     float4 *s_fj = s_fr + 2;  // j-tile frames (hi, lo), double-buffered by tile parity
+    // The next j-tile goes by cp.async into this thread's own landing slots
+    // (s_raw[u * 128 + tid], zero-filled past j1); at the tile start each
+    // thread moves its own slots into the SoA tile, so s_raw needs no barrier.
     auto fetch = [&](int jt) {
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int j = jt + u * kPairThreads + tid;
-            pre[u] = j < j1 ? d.sh32[e_start + j] : make_float4(kSentinel, kSentinel, kSentinel, 0.f);
+            cp_async16_zfill(s_raw + u * kPairThreads + tid, d.sh32 + e_start + (j < j1 ? j : j0),
+                             j < j1 ? 16u : 0u);
         }
         if (TF && tid < 2)  // jt is a tile start (j-chunks are whole tiles)
             cp_async16(s_fj + 2 * ((jt / TJ) & 1) + tid,
@@ -127,8 +130,8 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
     };
     fetch(j0);
     for (int jt = j0; jt < j1; jt += TJ) {
-        if (TF && tid < 2) cp_async_wait_all();  // this tile's frame has landed
-        __syncthreads();  // the previous tile has been consumed
+        cp_async_wait_all();  // this thread's slots of the tile (and the tile's frame) have landed
+        __syncthreads();      // the previous tile has been consumed
         float ox = 0.f, oy = 0.f, oz = 0.f;
         if (TF) {  // this j-tile's frame relative to the item frame
             const int b = 2 * ((jt / TJ) & 1);
@@ -141,14 +144,16 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
         for (int u = 0; u < PER; ++u) {
             const int k = u * kPairThreads + tid;
             const float sc = H16 ? scale : 1.0f;  // exact (power of two)
+            float4 v = s_raw[k];
+            if (jt + k >= j1) v = make_float4(kSentinel, kSentinel, kSentinel, 0.f);
             if (TF) {
-                sx[k] = (pre[u].x + ox) * sc;
-                sy[k] = (pre[u].y + oy) * sc;
-                sz[k] = (pre[u].z + oz) * sc;
+                sx[k] = (v.x + ox) * sc;
+                sy[k] = (v.y + oy) * sc;
+                sz[k] = (v.z + oz) * sc;
             } else {
-                sx[k] = pre[u].x * sc;
-                sy[k] = pre[u].y * sc;
-                sz[k] = pre[u].z * sc;
+                sx[k] = v.x * sc;
+                sy[k] = v.y * sc;
+                sz[k] = v.z * sc;
             }
         }
         __syncthreads();
@@ -264,7 +269,7 @@ __device__ __forceinline__ int event_of_item(const int *__restrict__ base, int n
 }
 
 // Min blocks = 1 lets ptxas keep many independent pair chains in registers
-// (R = 4: ~246 registers, 2 blocks per SM); measured faster than letting it
+// (R = 4: ~240 registers, 2 blocks per SM); measured faster than letting it
 // trade registers for occupancy.
 // TF: the tile-frame variant (used when some event is large enough for one
 // lane per i-group); its small events still run the event-frame path.
@@ -272,6 +277,7 @@ template <int R, bool KAHAN, bool NEWTON, bool H16, bool TF>
 __global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
     __shared__ __align__(16) float s_x[kTileJ], s_y[kTileJ], s_z[kTileJ];
     __shared__ float4 s_fr[TF ? 6 : 1];  // tile frames: the item frame, then two j-tile frames
+    __shared__ __align__(16) float4 s_raw[kTileJ];  // cp.async landing slots of the next j-tile
     __shared__ int s_item;
     Ctrl *c = d.ctrl;
     if (step_skipped(c)) return;
@@ -289,10 +295,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
         const float scale = H16 ? h2_scale(__uint_as_float(ext[e])) : 1.0f;
         if (lanes_for(n_e, d.shape.small_n) == 1)
             pair_item_fp32_j<R, KAHAN, NEWTON, 1, H16, TF>(d, e_start, n_e, local, scale, s_x, s_y,
-                                                           s_z, s_fr);
+                                                           s_z, s_fr, s_raw);
         else
             pair_item_fp32_j<R, KAHAN, NEWTON, 4, H16, false>(d, e_start, n_e, local, scale, s_x, s_y,
-                                                              s_z, s_fr);
+                                                              s_z, s_fr, s_raw);
         __syncthreads();  // s_item and the tiles are reused by the next item
     }
 }
