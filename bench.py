@@ -308,7 +308,7 @@ def main():
                     help="run on a random sub-sample of the bundle (profiling small cases)")
     ap.add_argument("--pair-R", type=int, default=0, help="force the pair-kernel register blocking")
     ap.add_argument("--tile-frames", type=int, default=0, choices=[0, 1],
-                    help="FP32 shadow relative to 256-slot tile origins for events of >= 8192 holes")
+                    help="FP32 shadow relative to 256-slot tile origins for events of >= 2048 holes")
     ap.add_argument("--workload", default="bundle", choices=sorted(WORKLOADS))
     ap.add_argument("--to-completion", action="store_true",
                     help="time one run until every hole is collected (graphs, no per-step flush)")

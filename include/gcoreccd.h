@@ -86,7 +86,7 @@ typedef struct {
                               still moving (Sec. 1): pixel count q = q charges at the pixel centre
                               at depth stored_z_um, softened as in Eq. 6; the image at the start of
                               each step; off-image charge is not stored */
-    int32_t tile_frames;   /* 1 (FP32 forms): events of >= 8192 holes are ordered along a Morton
+    int32_t tile_frames;   /* 1 (FP32 forms): events of >= 2048 holes are ordered along a Morton
                               curve at load and their FP32 shadow is taken relative to the FP64
                               origin of each 256-slot tile instead of the event centroid, so close
                               pairs keep ~2^-24 of their tile's extent rather than of the event's;

@@ -31,9 +31,11 @@ constexpr int kChunkThreads = 1024; // threads per integrate/compact block
 constexpr int kPairThreads = 128;   // threads per pair-kernel block
 constexpr int kTileJ = 256;         // j positions staged in shared memory per tile
 constexpr float kSentinel = 1.0e15f; // padding position: its Eq. 6 term rounds to 0
-constexpr int kSmallEvent = 8192;    // FP32 forms: smaller events split j over 4 lanes and use
+constexpr int kSmallEvent = 2048;    // FP32 forms: smaller events split j over 4 lanes and use
                                      // the event frame; larger ones one lane (and, with
-                                     // tile_frames, tile frames)
+                                     // tile_frames, tile frames).  Measured on 4096 X-ray
+                                     // events (267..4800 holes): 2048 is 4.7 % faster than
+                                     // 8192 and keeps a 1573-hole event on 4 lanes
 
 // Control block: one per simulation, written only by the device during a run.
 struct Ctrl {

@@ -59,9 +59,13 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
     constexpr int G = 32 / L;
     constexpr int STRIDE = kPairThreads / L;
     constexpr int IB = R * STRIDE;
-    constexpr int TJ = kTileJ;               // j positions per shared-memory tile
+    // j positions per shared-memory tile: 4 lanes split a tile, so the 4-lane
+    // path takes 4 tiles' worth at once (measured +3.4 % on 4096 X-ray events)
+    constexpr int TJ = L == 1 ? kTileJ : 4 * kTileJ;
     constexpr int PER = TJ / kPairThreads;
-    constexpr int JU = 2;             // 16-byte loads (4 j's) per coordinate per iteration
+    // 16-byte loads (4 j's) per coordinate per iteration; the 4-lane path needs
+    // more loads in flight to cover shared-memory latency (measured: 4 > 2, 8)
+    constexpr int JU = L == 1 ? 2 : 4;
     constexpr int STEP = 4 * JU * L;  // j's consumed per unrolled iteration by the L lanes
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane / L, ph = lane % L;
@@ -275,9 +279,9 @@ __device__ __forceinline__ int event_of_item(const int *__restrict__ base, int n
 // lane per i-group); its small events still run the event-frame path.
 template <int R, bool KAHAN, bool NEWTON, bool H16, bool TF>
 __global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
-    __shared__ __align__(16) float s_x[kTileJ], s_y[kTileJ], s_z[kTileJ];
+    __shared__ __align__(16) float s_x[4 * kTileJ], s_y[4 * kTileJ], s_z[4 * kTileJ];
     __shared__ float4 s_fr[TF ? 6 : 1];  // tile frames: the item frame, then two j-tile frames
-    __shared__ __align__(16) float4 s_raw[kTileJ];  // cp.async landing slots of the next j-tile
+    __shared__ __align__(16) float4 s_raw[4 * kTileJ];  // cp.async landing slots of the next j-tile
     __shared__ int s_item;
     Ctrl *c = d.ctrl;
     if (step_skipped(c)) return;
