@@ -671,6 +671,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         GC_CUDA(cudaMemsetAsync(d.occ_cnt, 0, E * 4, st));
     }
     GC_CUDA(cudaMemsetAsync(d.collect_step, 0xFF, N * 4, st));
+    GC_CUDA(cudaMemsetAsync(d.chunk_cnt, 0, nchunk * 4, st));  // the step-0 pass may accumulate
     GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, st));
     GC_CUDA(cudaMemsetAsync(d.image, 0, img * 4, st));
     GC_CUDA(cudaMemsetAsync(d.off_image, 0, E * 8, st));
@@ -683,7 +684,10 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     s->h_ctrl->n_active = (int)n;
     GC_CUDA(cudaMemcpyAsync(d.ctrl, s->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
 
-    s->integ_grid = std::max(1, std::min((int)nchunk, 2 * s->sm_count));
+    // integrate/compact grid: one block per chunk (per 256-slot unit while few chunks
+    // are active), at most two waves of blocks
+    const int units0 = (int)nchunk * (fine_units((int)n) ? kChunk / kFineUnit : 1);
+    s->integ_grid = std::max(1, std::min(units0, 2 * s->sm_count));
     const bool f64 = fp64_mode(s);
     if (n > 0) {
         // step 0: reflect at the back surface, collect what is already in the well
@@ -946,6 +950,7 @@ gc_status gc_restore_state(gc_sim *s, const gc_state *st) {
     GC_CUDA(cudaMemcpyAsync(d.act[0], act.data(), (size_t)pos * 4, cudaMemcpyHostToDevice, q));
     GC_CUDA(cudaMemcpyAsync(d.ev_off[0], ioff.data(), (E + 1) * 4, cudaMemcpyHostToDevice, q));
     GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, q));
+    GC_CUDA(cudaMemsetAsync(d.chunk_cnt, 0, (size_t)ceil_div((int)std::max<int64_t>(n, 1), kChunk) * 4, q));
     GC_CUDA(cudaStreamSynchronize(q));
     Ctrl c{};
     c.step = st->step;

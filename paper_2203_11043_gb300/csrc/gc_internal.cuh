@@ -117,6 +117,13 @@ struct Dev {
 
 // Number of lanes sharing one i-group in the pair kernel for an event of n
 // active carriers, and the i-tile length that follows from it.
+// Integrate: with at most kFineMaxChunks chunks active, each chunk is split
+// into kFineUnit-slot units so that a small step spreads over many SMs (the
+// per-hole FP64 update would otherwise run on one SM); chunk counts are then
+// accumulated with atomics into counters the finalize kernel has zeroed.
+constexpr int kFineUnit = 256;
+constexpr int kFineMaxChunks = 8;
+__host__ __device__ inline bool fine_units(int n_act) { return (n_act + kChunk - 1) / kChunk <= kFineMaxChunks; }
 __host__ __device__ inline int lanes_for(int n, int small_n) { return n < small_n ? 4 : 1; }
 __host__ __device__ inline int itile_for(int R, int lanes) { return R * kPairThreads / lanes; }
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

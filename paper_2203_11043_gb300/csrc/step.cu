@@ -364,15 +364,28 @@ __global__ void __launch_bounds__(kChunkThreads) integrate_kernel(Dev d) {
             d.ev_ext[cur ^ 1][e] = 0u;
     }
     const int nchunks = ceil_div(n_act, kChunk);
-    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const bool fine = fine_units(n_act);  // uniform over the grid
+    const int per_chunk = fine ? kChunk / kFineUnit : 1;
+    for (int u = blockIdx.x; u < nchunks * per_chunk; u += gridDim.x) {
+        const int ch = u / per_chunk;
         int kept = 0;
+        if (fine) {  // one slot per thread of the first kFineUnit threads
+            if (threadIdx.x < kFineUnit) {
+                const int p = ch * kChunk + (u - ch * per_chunk) * kFineUnit + threadIdx.x;
+                const bool keep = p < n_act ? advance_slot<F64, INIT>(d, cur, p, step) : false;
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) d.keepmask[p >> 5] = m;
+                kept = __popc(m);
+            }
+        } else {
 #pragma unroll
-        for (int k = 0; k < kChunk / kChunkThreads; ++k) {
-            const int p = ch * kChunk + k * kChunkThreads + threadIdx.x;
-            const bool keep = p < n_act ? advance_slot<F64, INIT>(d, cur, p, step) : false;
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) d.keepmask[p >> 5] = m;
-            kept += __popc(m);
+            for (int k = 0; k < kChunk / kChunkThreads; ++k) {
+                const int p = ch * kChunk + k * kChunkThreads + threadIdx.x;
+                const bool keep = p < n_act ? advance_slot<F64, INIT>(d, cur, p, step) : false;
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) d.keepmask[p >> 5] = m;
+                kept += __popc(m);
+            }
         }
         if (lane == 0) s_cnt[warp] = kept;
         __syncthreads();
@@ -380,7 +393,10 @@ __global__ void __launch_bounds__(kChunkThreads) integrate_kernel(Dev d) {
             int v = s_cnt[lane];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) d.chunk_cnt[ch] = v;
+            if (lane == 0) {
+                if (fine) atomicAdd(&d.chunk_cnt[ch], v);
+                else d.chunk_cnt[ch] = v;
+            }
         }
         __syncthreads();
     }
@@ -524,6 +540,8 @@ __global__ void __launch_bounds__(kChunkThreads) finalize_kernel(Dev d) {
     const long long tot_cs = dummy;
     (void)tot_pairs_ex;
     (void)tot_cs_ex;
+    // the next integrate accumulates its chunk counts atomically: zero them
+    if (fine_units((int)carry_n) && threadIdx.x < ceil_div((int)carry_n, kChunk)) d.chunk_cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         noff[d.n_events] = (int)carry_n;
         d.item_base[d.n_events] = (int)carry_items;
