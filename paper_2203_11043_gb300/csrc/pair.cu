@@ -59,13 +59,16 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
     constexpr int G = 32 / L;
     constexpr int STRIDE = kPairThreads / L;
     constexpr int IB = R * STRIDE;
-    // j positions per shared-memory tile: 4 lanes split a tile, so the 4-lane
-    // path takes 4 tiles' worth at once (measured +3.4 % on 4096 X-ray events)
-    constexpr int TJ = L == 1 ? kTileJ : 4 * kTileJ;
+    // j positions per shared-memory tile (a multiple of the 256-slot frame
+    // tile): tile frames need one frame per staged tile; otherwise longer tiles
+    // amortise the barriers (4 lanes split a tile, so the 4-lane path takes 4
+    // tiles' worth).  Measured on 4096 X-ray events: +3.4 % for the 4-lane path.
+    constexpr int TJ = L == 1 ? (TF ? kTileJ : 2 * kTileJ) : 4 * kTileJ;
     constexpr int PER = TJ / kPairThreads;
-    // 16-byte loads (4 j's) per coordinate per iteration; the 4-lane path needs
-    // more loads in flight to cover shared-memory latency (measured: 4 > 2, 8)
-    constexpr int JU = L == 1 ? 2 : 4;
+    // 16-byte loads (4 j's) per coordinate per iteration: about 16 packed
+    // pair chains in flight per lane (R * JU * 2 = 16 on one lane; the 4-lane
+    // path measured best at 4 for R = 2, against 2 and 8)
+    constexpr int JU = L == 1 ? (R >= 8 ? 1 : 8 / R) : 4;
     constexpr int STEP = 4 * JU * L;  // j's consumed per unrolled iteration by the L lanes
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane / L, ph = lane % L;

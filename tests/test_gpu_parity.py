@@ -7,8 +7,9 @@ Tolerances:
     arithmetic (unit roundoff u = 2^-24): per term ~12 u from the operations
     plus the rounding of the FP32 shadow positions (|coordinate| <= rho
     relative to the event origin) amplified by 1/sqrt(d^2 + eps^2); the sum
-    adds (tile length + 16) u of sum_j |term_j| with Kahan across tiles, or
-    (n + 16) u without it.
+    adds (b + 16) u of sum_j |term_j| with Kahan across tiles, where b = 256 is
+    the most terms one FP32 accumulator sums between folds, or (n + 16) u
+    without it.
   * FP16x2 form: r^2 is formed from f16 differences (three roundings of
     2^-11 each on the squares and sums) so each term carries a relative error
     up to 1.5 * 6 * 2^-11 in r^-3, plus 1.5 * 2^-25 / (r^2 s^2) where r^2 s^2
@@ -27,7 +28,10 @@ from paper_2203_11043_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
-TILE_J = 256
+# FP32 terms summed by one accumulator between Kahan folds: one lane sums a
+# 512-j tile as even-j and odd-j halves (256 each); four lanes split a
+# 1024-j tile (128 per half); a tile-frame item stages 256-j tiles (128)
+KAHAN_BLOCK = 256
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +68,7 @@ def field_bound(xyz, targets, precision, eps=0.01):
         if precision == 0:
             out[k] = 1e-12 * K * mag.sum() + 1e-300
             continue
-        acc = (n + 16) if precision == 1 else (TILE_J + 16)
+        acc = (n + 16) if precision == 1 else (KAHAN_BLOCK + 16)
         per = mag * (12 * U32 + 20 * U32 * rho / np.sqrt(s2))
         if precision == 3:
             sc = 2.0 ** np.floor(np.log2(52.0 / max(rho, 1e-6)))
