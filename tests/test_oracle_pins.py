@@ -416,3 +416,24 @@ def test_stored_charge_broadens_the_image():
         sim.run()
         sig.append(np.hypot(sim.x.std(), sim.y.std()))
     assert sig[1] > sig[0] * 1.001
+
+
+def test_step_targets_matches_a_committed_step():
+    """The sampled large-N parity tests take their expected positions from
+    step_targets.  It shares the field and update routines with orc_run, so
+    this is no physics pin: it checks the helper's own indexing (targets,
+    sources, step counter, per-event random-number index) against a committed
+    step of a single event, bit for bit, for every hole active before it."""
+    rng = np.random.default_rng(12)
+    xyz = np.array([0.0, 0.0, 4.0]) + 1.5 * rng.standard_normal((300, 3))
+    xyz[:5, 2] = 674.0 + rng.random(5)                  # near the back surface: reflections
+    p = O.make_params(img_w=16, img_h=16)
+    sim = O.Simulation(p, xyz, seeds=np.array([77], dtype=np.uint64))
+    sim.run(3)
+    x0 = sim.positions().copy()
+    active = np.nonzero(sim.collect_step < 0)[0]
+    assert 0 < len(active) < len(xyz)
+    want = O.step_targets(p, x0, active, active, 77, sim.step + 1)
+    sim.run(1)
+    assert np.any(sim.collect_step == sim.step)          # some holes were collected in this step
+    assert np.array_equal(sim.positions()[active], want)
