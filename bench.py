@@ -9,7 +9,8 @@ update, collection, binning), compaction and bookkeeping.
 Prints ONE JSON line: pair-interactions/s (value) and carrier-steps/s, the
 pair kernel's live roofline fraction, the oracle CPU baseline, an end-to-end
 figure through the C ABI with host buffers, clocks sampled during the timed
-region, and the FP64 form timed on a sub-sample of the same workload.
+region, the FP64 form timed on a sub-sample of the same workload, and the
+batched X-ray workload (4096 events) with its batched-vs-per-event ratio.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -95,20 +96,25 @@ def replica_seeds(seeds, rank: int):
 
 
 def recorded_traffic():
-    """DRAM bytes per pair-kernel launch from the committed ncu summary of the
-    track-bundle workload, only while the kernel source is the one that was
-    profiled (otherwise None)."""
+    """DRAM bytes per pair-kernel launch on the track-bundle workload, as
+    recorded from one ncu capture in profiles/pair_fp32_track_bundle_traffic.txt
+    (key=value lines), only while the kernel source is the one that was
+    profiled (otherwise None): a recorded figure, not measured by this run."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "pair_fp32_track_bundle_traffic.md")
+    path = os.path.join(ROOT, "profiles", "pair_fp32_track_bundle_traffic.txt")
     try:
-        text = open(path).read()
+        rec = {}
+        for line in open(path):
+            line = line.split("#", 1)[0].strip()
+            if "=" in line:
+                k, v = line.split("=", 1)
+                rec[k.strip()] = v.strip()
         src = open(os.path.join(ROOT, "paper_2203_11043_gb300", "csrc", "pair.cu"), "rb").read()
     except OSError:
         return None
-    fields = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("traffic_", "kernel_")))
-    if fields.get("kernel_source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+    if rec.get("kernel_source_sha256") != hashlib.sha256(src).hexdigest():
         return None
-    return float(fields["traffic_bytes_per_launch"])
+    return float(rec["traffic_bytes_per_launch"])
 
 
 def measured_peaks():
@@ -295,6 +301,77 @@ def to_completion(args):
     return 0
 
 
+def batched_record(gc, stream, peak, steps=20, warmup=3, per_event=64):
+    """The batched X-ray workload (4096 independent events of 267..4800 holes,
+    Sec. 5.1's X-ray clouds) in one segmented launch per step: pair
+    interactions/s over its first `steps` steps (all events active) with the
+    pair kernel's own roofline fraction, and the same first `per_event` events
+    run to completion once as one batch and once as one simulation per event."""
+    import torch
+    wl = inputs.xray_batch()
+    p = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
+                             graph_steps=1, timing=1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin, stream=stream.cuda_stream) as sim:
+        for _ in range(warmup):
+            sim.run(1)
+        torch.cuda.synchronize()
+        b = sim.stats()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for a, z in ev:
+                flush.zero_()
+                a.record(stream)
+                sim.run(1)
+                z.record(stream)
+            torch.cuda.synchronize()
+        a_ = sim.stats()
+    ms = sum(a.elapsed_time(z) for a, z in ev)
+    pairs = a_["pair_interactions"] - b["pair_interactions"]
+    launches = a_["pair_kernel_launches"] - b["pair_kernel_launches"]
+    pair_ms = a_["pair_kernel_ms"] - b["pair_kernel_ms"]
+    achieved = pairs / (pair_ms / 1e3) if pair_ms > 0 else None
+    rec = {"workload": WORKLOADS["xray-batch"], "events": wl.n_events, "n_carriers": wl.n,
+           "steps": steps, "warmup": warmup, "pairs_per_s": pairs / (ms / 1e3),
+           "carrier_steps_per_s": (a_["carrier_steps"] - b["carrier_steps"]) / (ms / 1e3),
+           "ms_per_step": ms / steps, "pair_kernel_pairs_per_s": achieved,
+           "pair_kernel_frac": achieved / peak if achieved else None,
+           "pair_kernel_launches": launches, "pair_R": a_["pair_variant"], "jchunk": a_["jchunk"],
+           "pair_blocks": a_["pair_blocks"], "clocks": clk.summary(),
+           "l2": "flushed between timed steps (256 MB write)"}
+
+    def to_end(w):
+        q = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=w.img_w, img_h=w.img_h)
+        with gc.Simulation(q, w.xyz, w.ev_off, w.seeds, w.img_origin, stream=stream.cuda_stream) as s:
+            x, y = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            x.record(stream)
+            s.run(-1)
+            y.record(stream)
+            torch.cuda.synchronize()
+            return x.elapsed_time(y) / 1e3, s.stats()["pair_interactions"]
+
+    m = min(per_event, wl.n_events)
+    sub = inputs.Workload(wl.name, wl.xyz[:wl.ev_off[m]], wl.ev_off[:m + 1].copy(), wl.seeds[:m],
+                          wl.img_origin[:m], wl.img_w, wl.img_h)
+    bs, bp = to_end(sub)
+    tot, pp = 0.0, 0.0
+    for e in range(m):
+        lo, hi = int(wl.ev_off[e]), int(wl.ev_off[e + 1])
+        one = inputs.Workload(wl.name, wl.xyz[lo:hi], np.array([0, hi - lo], np.int64), wl.seeds[e:e + 1],
+                              wl.img_origin[e:e + 1], wl.img_w, wl.img_h)
+        es, ep = to_end(one)
+        tot += es
+        pp += ep
+    rec["per_event_launches"] = {
+        "events": m, "mode": "each to completion, CUDA graphs with the device-side loop",
+        "batched_pairs_per_s": bp / bs, "per_event_pairs_per_s": pp / tot,
+        "batched_seconds": bs, "per_event_seconds": tot,
+        "batched_over_per_event": (bp / bs) / (pp / tot)}
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,6 +381,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched X-ray sub-record of the default run")
     ap.add_argument("--n-carriers", type=int, default=0,
                     help="run on a random sub-sample of the bundle (profiling small cases)")
     ap.add_argument("--pair-R", type=int, default=0, help="force the pair-kernel register blocking")
@@ -393,6 +472,8 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pairs/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "traffic_source": "recorded from one ncu capture of this kernel source "
+                                  "(profiles/pair_fp32_track_bundle_traffic.txt), not measured by this run",
                 "kernel": "pair_fp32_kernel<R,Kahan>",
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz "
                               f"(sm_max_mhz of MEASURED_PEAKS.json) / {FP32_OPS_PER_PAIR} FP32 ops per pair",
@@ -472,6 +553,10 @@ def main():
                        "steps": e2e_steps,
                        "includes": "gc_create + gc_load_carriers (host positions) + gc_run + gc_collect + "
                                    "gc_image (host outputs), host wall clock"}
+
+    if not args.no_batched and rank == 0 and args.coulomb and args.workload == "bundle" \
+            and not args.n_carriers:
+        line["batched"] = batched_record(gc, stream, peak)
 
     if not args.no_cpu_baseline and rank == 0 and world == 1 and args.coulomb:
         line["cpu_baseline"] = cpu_baseline(wl)

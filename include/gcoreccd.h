@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define GC_ABI_VERSION 1u
+#define GC_ABI_VERSION 2u
 
 typedef enum {
     GC_OK = 0,
@@ -92,6 +92,12 @@ typedef struct {
                               pairs keep ~2^-24 of their tile's extent rather than of the event's;
                               costs a few percent of pair-kernel throughput; 0 = event frame */
     double stored_z_um;    /* depth of the stored-charge points */
+    int32_t fuse_small;    /* 1: while at most 8192 holes are active, each step is two launches (a
+                              pair kernel that also integrates every i-tile once its last j-chunk
+                              is summed, then one block that compacts); same results as the
+                              four-launch step.  Not used with newton, tile frames, stored charge
+                              or timing */
+    int32_t reserved0;
 } gc_params;
 
 typedef struct gc_sim gc_sim;
@@ -114,16 +120,18 @@ typedef struct {
     int64_t timed_steps;          /* with timing on: steps whose kernels were timed */
     int32_t device_loop;          /* 1: gc_run is one graph launch with a device-side loop
                                      (conditional WHILE node over passes of graph_steps steps) */
-    int32_t reserved;
+    int32_t fused_path;           /* 1: the last gc_run ran steps on the fused small-workload path */
 } gc_stats;
 
 /* Defaults: the CCD of the X-ray and muon workloads (thickness 675 um,
  * well at z = 0, a1 = 2 V/(cm um), a2 = 1500 V/cm, T = 140 K,
  * eps_Si = 11.7, eps = 0.01 um, dt = 10 ps, 15 um pixels on 64 x 64,
- * FP32 + Kahan, graphs of 32 steps, autotune on, timing off). */
+ * FP32 + Kahan, graphs of 32 steps, autotune on, timing off, fused small
+ * steps on). */
 void gc_default_params(gc_params *p);
 
-/* Validate `p` and create an empty simulation bound to the current CUDA
+/* Validate `p` (the Sec. 3.2 parameter list) and create an empty simulation
+ * bound to the current CUDA
  * device and to `cuda_stream` (a cudaStream_t; NULL = a stream the library
  * creates and owns).  *out receives the handle.  GC_ERR_PARAM for an invalid
  * parameter (checked before any CUDA call); GC_ERR_NO_DEVICE without a GPU. */
@@ -151,8 +159,10 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n,
  * still active.  The call returns after the device has finished. */
 gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done);
 
-/* Copy out the collection results, in original carrier order (all host
- * pointers, each nullable): final_xy [n][2] (position at collection; current
+/* Copy out the collection results of the Fig. 2 z check -- the x-y position
+ * at which each hole reached the wells, the data of the Sec. 5.1 / Fig. 5
+ * histograms -- in original carrier order (all host pointers, each
+ * nullable): final_xy [n][2] (position at collection; current
  * x, y for carriers still active), collect_step [n] (step of collection, 0 for
  * carriers in the well at load, -1 if still active), n_collected /
  * n_offimage / n_active [n_events] per event. */
@@ -164,7 +174,8 @@ gc_status gc_collect(gc_sim *s, double *final_xy, int32_t *collect_step,
  * is_device != 0: `img` is a device pointer on this simulation's device. */
 gc_status gc_image(gc_sim *s, uint32_t *img, int is_device);
 
-/* Current positions [n][3] (host), original carrier order. */
+/* Current positions [n][3] (host), original carrier order: the final
+ * results that Sec. 3.2 saves to a file at the end of a run. */
 gc_status gc_positions(gc_sim *s, double *xyz);
 
 /* Device counters (host struct). */
@@ -210,22 +221,27 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
  * running inside an allocator or memory pool it must not re-enter, inside a
  * framework that owns every device byte, or after a start-up phase beyond
  * which allocation is not allowed.  Same arguments, units, layout and result
- * (up to the order of FP32 rounding) as gc_coulomb_field; the paper has no
- * counterpart of this entry point.  It calls no cudaMalloc, cudaFree or
- * other allocating routine: its scratch (about 4.2 MB) is a fixed device array
- * inside the library, held by every GPU that loads it until the process
- * exits.  n above GC_NOALLOC_MAX_CARRIERS returns GC_ERR_PARAM.  The first
- * call on each device looks up that array's device address (with the device
- * current), so make that first call before any stream capture.  Every call
- * shares the array and finds the previous call's contents there; the call
- * resets what must start from zero, but calls whose work overlaps on the GPU
- * (other streams or host threads) race and must be serialised by the caller.
- * Returns after the device has finished. */
+ * as gc_coulomb_field (bit for bit in the FP64 form and, for the FP32 forms,
+ * up to the order of the per-chunk partial sums whenever the scratch forces
+ * longer j-chunks); every gc_precision is accepted.  The paper has no
+ * counterpart of this entry point.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch (about 7.3 MB: control block, the position
+ * shadow and the per-chunk partial sums) is a fixed device array inside the
+ * library, held by every GPU that loads it until the process exits.  n above
+ * GC_NOALLOC_MAX_CARRIERS returns GC_ERR_PARAM.  The first call on each device
+ * looks up that array's device address (with the device current), so make
+ * that first call before any stream capture.  Every call shares the array and
+ * finds the previous call's contents there; the call resets what must start
+ * from zero, but calls whose work overlaps on the GPU (other streams or host
+ * threads) race and must be serialised by the caller.  The call synchronizes
+ * `cuda_stream` before it returns; a failed CUDA call returns its status with
+ * the text in gc_last_cuda_error. */
 gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, double softening_um,
                                    double eps_si_rel, int32_t precision, double *E_dev,
                                    void *cuda_stream);
 
-/* Free everything owned by the simulation (NULL is a no-op). */
+/* Free everything owned by the simulation (NULL is a no-op); the end of the
+ * Sec. 3.2 run, after which no result of `s` can be read. */
 void gc_destroy(gc_sim *s);
 
 /* Static, human-readable name of a status code. */

@@ -21,9 +21,10 @@
 using namespace gc;
 
 namespace {
-
 thread_local char g_cuda_err[256] = "";
+}  // namespace
 
+namespace gc {
 gc_status cuda_fail(cudaError_t e) {
     std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e),
                   cudaGetErrorString(e));
@@ -31,6 +32,9 @@ gc_status cuda_fail(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return GC_ERR_ALLOC;
     return GC_ERR_CUDA;
 }
+}  // namespace gc
+
+namespace {
 
 #define GC_CUDA(call)                                  \
     do {                                               \
@@ -65,7 +69,7 @@ gc_status validate(const gc_params *p) {
     if (p->graph_steps < 0 || p->graph_steps > 4096) return GC_ERR_PARAM;
     if (p->jchunk < 0) return GC_ERR_PARAM;
     if ((p->coulomb | p->diffusion | p->reflect_back | p->autotune | p->newton | p->timing |
-         p->stored_charge | p->tile_frames) & ~1)
+         p->stored_charge | p->tile_frames | p->fuse_small) & ~1)
         return GC_ERR_PARAM;
     if (p->pair_R != 0 && p->pair_R != 2 && p->pair_R != 4 && p->pair_R != 8) return GC_ERR_PARAM;
     return GC_OK;
@@ -152,23 +156,25 @@ void morton_order(const double *xyz, int *ids, int n) {
     for (int k = 0; k < n; ++k) ids[k] = key[k].second;
 }
 
+}  // namespace
+
 // j-chunk length: one chunk per event when the i-tiles alone give every
 // resident block >= 32 items; otherwise split j so that they do (at most 32
 // chunks), keeping dynamic-scheduling tail loss near 1/64 of a step.
-int choose_jchunk(const std::vector<long long> &sizes, int R, int small_n, int slots, int user) {
+int gc::choose_jchunk(const std::vector<long long> &sizes, const PairShape &sh, int user, int gran) {
     long long n_max = 1;
     for (long long n : sizes) n_max = std::max(n_max, n);
-    if (user > 0) return round_up(user, kTileJ);
+    if (user > 0) return round_up(user, gran);
     long long tiles = 0;
     for (long long n : sizes)
-        if (n > 0) tiles += (n + itile_for(R, lanes_for((int)n, small_n)) - 1) /
-                            itile_for(R, lanes_for((int)n, small_n));
-    const long long want = 32LL * std::max(slots, 1);
+        if (n > 0) {
+            const int it = itile_for(sh.R, lanes_for(sh, (int)n));
+            tiles += (n + it - 1) / it;
+        }
+    const long long want = 32LL * std::max(sh.n_blocks, 1);
     long long js = tiles >= want ? 1 : std::min<long long>(32, (want + tiles - 1) / std::max(tiles, 1LL));
-    return round_up((n_max + js - 1) / js, kTileJ);
+    return round_up((n_max + js - 1) / js, gran);
 }
-
-}  // namespace
 
 struct gc_sim {
     gc_params p;
@@ -186,6 +192,13 @@ struct gc_sim {
     long long *h_limit = nullptr;    // pinned staging for step_limit and loop_last
     cudaGraphExec_t graph = nullptr;
     bool graph_loops = false;        // the graph holds a device-side WHILE loop over K-step passes
+    // fused small-workload path: two launches per step while at most kFusedMax
+    // holes are active (its own graph; the unfused graph hands over to it)
+    bool fused_ok = false;
+    int fused_grid = 0;
+    bool fused_ran = false;          // the last gc_run used the fused path
+    cudaGraphExec_t graph_small = nullptr;
+    bool small_loops = false;
     int integ_grid = 1;
     int launches_per_step = 0;
     long long part_cap_chunks = 1;   // j-chunks the partial buffer can hold
@@ -205,10 +218,13 @@ bool fp64_mode(const gc_sim *s) { return s->p.precision == GC_FP64; }
 bool use_graph(const gc_sim *s) { return s->p.graph_steps > 0 && !s->p.timing; }
 
 void free_state(gc_sim *s) {
-    if (s->graph) {
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-    }
+    for (cudaGraphExec_t *g : {&s->graph, &s->graph_small})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+    s->fused_ok = false;
+    s->fused_ran = false;
     for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
         for (cudaEvent_t e : *v) cudaEventDestroy(e);
         v->clear();
@@ -221,8 +237,14 @@ void free_state(gc_sim *s) {
 }
 
 // One time step; k indexes the step inside a captured graph (timing events).
-gc_status enqueue_step(gc_sim *s, int k) {
+// fused: the two-launch small-workload step.
+gc_status enqueue_step(gc_sim *s, int k, bool fused) {
     const bool f64 = fp64_mode(s);
+    if (fused) {
+        GC_CUDA(launch_fused_pair(s->dev, s->p.precision, s->fused_grid, s->stream));
+        GC_CUDA(launch_small_tail(s->dev, f64, s->stream));
+        return GC_OK;
+    }
     const bool timed = s->p.timing && k < (int)s->ev_a.size();
     if (timed) GC_CUDA(cudaEventRecord(s->ev_a[k], s->stream));
     if (s->phys.coulomb) GC_CUDA(launch_pair(s->dev, s->p.precision, s->p.newton, s->stream));
@@ -233,7 +255,7 @@ gc_status enqueue_step(gc_sim *s, int k) {
     GC_CUDA(launch_compact(s->dev, f64, s->integ_grid, s->stream));
     if (timed) GC_CUDA(cudaEventRecord(s->ev_d[k], s->stream));
     GC_CUDA(launch_finalize(s->dev, false, s->stream));
-    if (s->dev.tile_frames) GC_CUDA(launch_shadow(s->dev, s->stream));
+    if (s->dev.tile_frames) GC_CUDA(launch_shadow(s->dev, s->sm_count, s->stream));
     return GC_OK;
 }
 
@@ -256,24 +278,26 @@ gc_status set_limit(gc_sim *s, long long limit) {
 // body is K steps plus the loop-condition kernel, so a whole gc_run is one
 // graph launch with no host round trip; otherwise a plain graph of K steps
 // that gc_run launches repeatedly.
-gc_status capture_plain_graph(gc_sim *s) {
+gc_status capture_plain_graph(gc_sim *s, bool fused, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     GC_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     gc_status st = GC_OK;
-    for (int k = 0; k < s->p.graph_steps && st == GC_OK; ++k) st = enqueue_step(s, k);
+    for (int k = 0; k < s->p.graph_steps && st == GC_OK; ++k) st = enqueue_step(s, k, fused);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (st != GC_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e);
-    e = cudaGraphInstantiate(&s->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e);
     return GC_OK;
 }
 
-bool capture_loop_graph(gc_sim *s) {
+// The unfused loop stops once the fused graph can take over.
+bool capture_loop_graph(gc_sim *s, bool fused, cudaGraphExec_t *outg) {
+    cudaGraphExec_t &graph = *outg;
     cudaGraph_t g = nullptr, body = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
     bool ok = false;
@@ -292,50 +316,102 @@ bool capture_loop_graph(gc_sim *s) {
                                           cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             break;
         gc_status st = GC_OK;
-        for (int k = 0; k < s->p.graph_steps && st == GC_OK; ++k) st = enqueue_step(s, k);
-        const cudaError_t le = st == GC_OK ? launch_loop_cond(s->dev, h, s->stream) : cudaErrorUnknown;
+        for (int k = 0; k < s->p.graph_steps && st == GC_OK; ++k) st = enqueue_step(s, k, fused);
+        const int switch_below = (!fused && s->fused_ok) ? kFusedMax : 0;
+        const cudaError_t le =
+            st == GC_OK ? launch_loop_cond(s->dev, h, switch_below, s->stream) : cudaErrorUnknown;
         cudaGraph_t out = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(s->stream, &out);
         if (st != GC_OK || le != cudaSuccess || ee != cudaSuccess) break;
-        if (cudaGraphInstantiate(&s->graph, g, 0) != cudaSuccess) break;
+        if (cudaGraphInstantiate(&graph, g, 0) != cudaSuccess) break;
         ok = true;
     } while (0);
     cudaGraphDestroy(g);
     if (!ok) {
-        if (s->graph) cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
         cudaGetLastError();  // clear a failed attempt; the plain graph is used instead
     }
     return ok;
 }
 
+// The graphs a gc_run launches: the unfused step loop (unless every step is
+// small enough for the fused path) and the fused one (when available).
 gc_status capture_graph(gc_sim *s) {
-    if (s->graph) {
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-    }
-    s->graph_loops = false;
+    for (cudaGraphExec_t *g : {&s->graph, &s->graph_small})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+    s->graph_loops = s->small_loops = false;
     if (!use_graph(s)) return GC_OK;
-    if (capture_loop_graph(s)) {
-        s->graph_loops = true;
-        return GC_OK;
+    if (!s->fused_ok || s->h_ctrl->n_active > kFusedMax) {
+        if (capture_loop_graph(s, false, &s->graph)) {
+            s->graph_loops = true;
+        } else {
+            gc_status r = capture_plain_graph(s, false, &s->graph);
+            if (r != GC_OK) return r;
+        }
     }
-    return capture_plain_graph(s);
+    if (s->fused_ok) {
+        if (capture_loop_graph(s, true, &s->graph_small)) {
+            s->small_loops = true;
+        } else {
+            gc_status r = capture_plain_graph(s, true, &s->graph_small);
+            if (r != GC_OK) return r;
+        }
+    }
+    return GC_OK;
 }
+
+// Shapes of the pair kernels.  FP64 form: one carrier per thread, 16 lanes
+// per carrier for small events, j-chunks of kTileJ64 granularity chosen like
+// the FP32 ones, lengthened if the partial buffer holds fewer chunks.
+PairShape fp64_shape(int sm_count, const std::vector<long long> &sizes, int user_jchunk, long long cap) {
+    PairShape sh{};
+    sh.R = 1;
+    sh.small_n = kSmallEvent;
+    sh.small_lanes = 16;
+    sh.n_blocks = sm_count * std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0, 0));
+    sh.jchunk = choose_jchunk(sizes, sh, user_jchunk, kTileJ64);
+    long long n_max = 1;
+    for (long long n : sizes) n_max = std::max(n_max, n);
+    if (cap > 0 && (n_max + sh.jchunk - 1) / sh.jchunk > cap)
+        sh.jchunk = round_up((n_max + cap - 1) / cap, kTileJ64);
+    return sh;
+}
+PairShape fp32_shape(int R, int sm_count, int precision, int newton, int tile_frames) {
+    PairShape sh{};
+    sh.R = R;
+    sh.small_n = kSmallEvent;
+    sh.small_lanes = 4;
+    sh.n_blocks = sm_count * std::max(1, pair_kernel_occupancy(precision, R, newton, tile_frames));
+    return sh;
+}
+
+}  // namespace
+
+// Shape of the standalone Eq. 6 evaluation of one event of n carriers; with
+// max_chunks > 0 the j-chunks are lengthened so that at most that many fit.
+PairShape gc::field_shape(int precision, int sm_count, long long n, long long max_chunks) {
+    const std::vector<long long> sizes{n};
+    if (precision == GC_FP64) return fp64_shape(sm_count, sizes, 0, max_chunks);
+    PairShape sh = fp32_shape(4, sm_count, precision, 0, 0);
+    sh.jchunk = choose_jchunk(sizes, sh, 0, kTileJ);
+    if (max_chunks > 0 && (n + sh.jchunk - 1) / sh.jchunk > max_chunks)
+        sh.jchunk = round_up((n + max_chunks - 1) / max_chunks, kTileJ);
+    return sh;
+}
+
+namespace {
 
 // Pick R (and the grid and j-chunk that follow from it) for the FP32 pair
 // kernel.  With autotune on, each candidate is timed on the loaded carriers.
 gc_status choose_shape(gc_sim *s, const std::vector<long long> &sizes) {
     PairShape best = s->dev.shape;
     if (fp64_mode(s)) {
-        const int occ = std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0, 0));
-        best.R = 1;
-        best.small_n = 0;
-        best.n_blocks = s->sm_count * occ;
-        long long n_max = 1;
-        for (long long n : sizes) n_max = std::max(n_max, n);
-        best.jchunk = round_up(n_max, kTileJ);  // one chunk: j summed in ascending order
-        s->dev.shape = best;
+        s->dev.shape = fp64_shape(s->sm_count, sizes, s->p.jchunk, s->part_cap_chunks);
+        GC_CUDA(launch_build_items(s->dev, s->stream));
         return GC_OK;
     }
     int cands[3] = {2, 4, 8};
@@ -349,13 +425,8 @@ gc_status choose_shape(gc_sim *s, const std::vector<long long> &sizes) {
         GC_CUDA(cudaEventCreate(&b));
     }
     for (int ci = first; ci <= last; ++ci) {
-        PairShape sh;
-        sh.R = cands[ci];
-        sh.small_n = kSmallEvent;
-        const int occ =
-            std::max(1, pair_kernel_occupancy(s->p.precision, sh.R, s->p.newton, s->dev.tile_frames));
-        sh.n_blocks = s->sm_count * occ;
-        sh.jchunk = choose_jchunk(sizes, sh.R, sh.small_n, sh.n_blocks, s->p.jchunk);
+        PairShape sh = fp32_shape(cands[ci], s->sm_count, s->p.precision, s->p.newton, s->dev.tile_frames);
+        sh.jchunk = choose_jchunk(sizes, sh, s->p.jchunk, kTileJ);
         long long n_max = 1;
         for (long long n : sizes) n_max = std::max(n_max, n);
         if ((n_max + sh.jchunk - 1) / sh.jchunk > s->part_cap_chunks) continue;
@@ -416,6 +487,7 @@ void gc_default_params(gc_params *p) {
     p->autotune = 1;
     p->newton = 0;
     p->jchunk = 0;
+    p->fuse_small = 1;
 }
 
 const char *gc_status_string(gc_status st) {
@@ -591,15 +663,22 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
 
     // partial-sum capacity: enough j-chunks for every autotune candidate
     long long cap = 1;
-    if (!fp64_mode(s) && s->phys.coulomb) {
+    if (fp64_mode(s) && s->phys.coulomb) {
+        const PairShape sh = fp64_shape(s->sm_count, sizes, s->p.jchunk, 0);
+        cap = (n_max + sh.jchunk - 1) / sh.jchunk;
+    } else if (s->phys.coulomb) {
         for (int R : {2, 4, 8}) {
-            const int occ = std::max(1, pair_kernel_occupancy(s->p.precision, R, s->p.newton, frames));
-            const int jc = choose_jchunk(sizes, R, kSmallEvent, s->sm_count * occ, s->p.jchunk);
+            const PairShape sh = fp32_shape(R, s->sm_count, s->p.precision, s->p.newton, frames);
+            const int jc = choose_jchunk(sizes, sh, s->p.jchunk, kTileJ);
             cap = std::max(cap, (n_max + jc - 1) / jc);
         }
     }
     s->part_cap_chunks = cap;
 
+    // the fused two-launch step for small workloads (not with the Newton
+    // step, tile frames, stored charge or per-kernel timing)
+    s->fused_ok = s->p.fuse_small && s->phys.coulomb && !s->phys.stored && !s->p.newton && !frames &&
+                  !s->p.timing && n > 0;
     Dev &d = s->dev;
     const size_t N = (size_t)std::max<int64_t>(n, 1);
     const size_t nchunk = (size_t)ceil_div((int)N, kChunk);
@@ -633,6 +712,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         occ_off[ie + 1] = occ_off[ie] + (int)std::min<long long>((long long)s->p.img_w * s->p.img_h, sizes[ie]);
     if (s->phys.stored) {
         GC_ALLOC(d.occ_pix, (size_t)std::max(occ_off[E], 1) * 4)
+        GC_ALLOC(d.occ_q, (size_t)std::max(occ_off[E], 1) * 4)
         GC_ALLOC(d.occ_f4, (size_t)std::max(occ_off[E], 1) * 16)
         GC_ALLOC(d.occ_off, (E + 1) * 4) GC_ALLOC(d.occ_cnt, E * 4)
     }
@@ -642,6 +722,11 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     GC_ALLOC(d.ev_seed, E * 8) GC_ALLOC(d.ev_origin, E * 24) GC_ALLOC(d.img_origin, E * 16)
     GC_ALLOC(d.ev_user, E * 4) GC_ALLOC(d.ev_first, E * 4) GC_ALLOC(d.image, img * 4)
     GC_ALLOC(d.off_image, E * 8)
+    if (s->fused_ok) {  // i-tiles are at least 8 carriers long
+        GC_ALLOC(d.tile_base, (E + 1) * 4)
+        GC_ALLOC(d.tile_ticket, (N / 8 + E + 1) * 4)
+        GC_ALLOC(d.keep8, N)
+    }
     GC_ALLOC(d.ctrl, sizeof(Ctrl))
 #undef GC_ALLOC
     d.part_stride = (long long)N;
@@ -649,7 +734,8 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     d.n_events = (int)E;
     d.phys = s->phys;
     d.shape.R = fp64_mode(s) ? 1 : 4;
-    d.shape.small_n = fp64_mode(s) ? 0 : small_n;
+    d.shape.small_n = small_n;
+    d.shape.small_lanes = fp64_mode(s) ? 16 : 4;
     d.tile_frames = frames ? 1 : 0;
     d.shape.jchunk = round_up(n_max, kTileJ);
     d.shape.n_blocks = s->sm_count;
@@ -675,6 +761,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, st));
     GC_CUDA(cudaMemsetAsync(d.image, 0, img * 4, st));
     GC_CUDA(cudaMemsetAsync(d.off_image, 0, E * 8, st));
+    if (d.tile_ticket) GC_CUDA(cudaMemsetAsync(d.tile_ticket, 0, (N / 8 + E + 1) * 4, st));
     if (d.ev_ext[0]) {
         GC_CUDA(cudaMemsetAsync(d.ev_ext[0], 0, E * 4, st));
         GC_CUDA(cudaMemsetAsync(d.ev_ext[1], 0, E * 4, st));
@@ -694,7 +781,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         GC_CUDA(launch_integrate(d, f64, true, s->integ_grid, st));
         GC_CUDA(launch_compact(d, f64, s->integ_grid, st));
         GC_CUDA(launch_finalize(d, true, st));
-        if (d.tile_frames) GC_CUDA(launch_shadow(d, st));
+        if (d.tile_frames) GC_CUDA(launch_shadow(d, s->sm_count, st));
     }
     GC_CUDA(cudaStreamSynchronize(st));
     gc_status r = read_ctrl(s);
@@ -703,11 +790,17 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         r = choose_shape(s, sizes);  // the sizes the partial buffer was sized for
         if (r != GC_OK) return r;
     }
+    if (s->fused_ok) {
+        s->fused_grid = s->sm_count * std::max(1, fused_pair_occupancy(s->p.precision, s->dev.shape.R));
+        if (!fused_pair_kernel_ptr(s->p.precision, s->dev.shape.R)) s->fused_ok = false;
+    }
     r = set_limit(s, 0);
     if (r != GC_OK) return r;
     r = read_ctrl(s);
     if (r != GC_OK) return r;
-    s->launches_per_step = (s->phys.coulomb ? 1 : 0) + (s->phys.stored ? 1 : 0) + (frames ? 1 : 0) + 3;
+    s->launches_per_step = (s->fused_ok && s->h_ctrl->n_active <= kFusedMax)
+                               ? 2
+                               : (s->phys.coulomb ? 1 : 0) + (s->phys.stored ? 1 : 0) + (frames ? 1 : 0) + 3;
     if (s->p.timing) {
         for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
             v->resize(1);
@@ -734,64 +827,78 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
     if (s->h_ctrl->n_active > 0 && step0 < limit) {
         gc_status r = set_limit(s, limit);
         if (r != GC_OK) return r;
-        const long long want = limit - step0;
         const int K = use_graph(s) ? s->p.graph_steps : 1;
-        // one launch = one captured graph of K steps, or one eager step
-        auto launch_one = [&]() -> gc_status {
-            const long long before = s->h_ctrl->step;
-            if (use_graph(s)) {
-                GC_CUDA(cudaGraphLaunch(s->graph, s->stream));
-            } else {
-                gc_status q = enqueue_step(s, 0);
-                if (q != GC_OK) return q;
-            }
-            if (s->p.timing) {  // read this launch's events before they are re-recorded
-                gc_status q = read_ctrl(s);
-                if (q != GC_OK) return q;
-                const long long did = std::min<long long>(K, s->h_ctrl->step - before);
-                for (long long k = 0; k < did; ++k) {
-                    float ms = 0.f;
-                    if (s->phys.coulomb) {
-                        GC_CUDA(cudaEventElapsedTime(&ms, s->ev_a[k], s->ev_b[k]));
-                        s->pair_ms += ms;
-                        s->pair_launches += 1;
-                    }
-                    GC_CUDA(cudaEventElapsedTime(&ms, s->ev_b[k], s->ev_c[k]));
-                    s->integ_ms += ms;
-                    GC_CUDA(cudaEventElapsedTime(&ms, s->ev_c[k], s->ev_d[k]));
-                    s->compact_ms += ms;
-                    s->timed_steps += 1;
-                }
-            }
-            return GC_OK;
-        };
-        if (s->graph_loops) {
-            // the device-side loop runs to the limit (or completion) in one launch
-            GC_CUDA(cudaGraphLaunch(s->graph, s->stream));
-            r = read_ctrl(s);
-            if (r != GC_OK) return r;
-        } else if (steps >= 0) {
-            // known step count: enqueue everything, synchronise once
-            for (long long k = 0; k < (want + K - 1) / K; ++k) {
-                r = launch_one();
-                if (r != GC_OK) return r;
-            }
-            r = read_ctrl(s);
-            if (r != GC_OK) return r;
-        } else {
-            // until every carrier is collected: poll between batches of steps
-            const long long batch = std::max(1, 256 / K);
-            for (;;) {
+        s->fused_ran = false;
+        // Up to two phases: the unfused step while more than kFusedMax holes
+        // are active, then (when available) the fused two-launch step.
+        for (int phase = 0; phase < 2; ++phase) {
+            const bool fz = s->fused_ok && s->h_ctrl->n_active <= kFusedMax;
+            if (fz) s->fused_ran = true;
+            cudaGraphExec_t g = fz ? s->graph_small : s->graph;
+            const bool loops = fz ? s->small_loops : s->graph_loops;
+            if (use_graph(s) && !g) return GC_ERR_STATE;
+            const long long want = limit - s->h_ctrl->step;
+            // one launch = one captured graph of K steps, or one eager step
+            auto launch_one = [&]() -> gc_status {
                 const long long before = s->h_ctrl->step;
-                for (long long k = 0; k < batch; ++k) {
+                if (use_graph(s)) {
+                    GC_CUDA(cudaGraphLaunch(g, s->stream));
+                } else {
+                    gc_status q = enqueue_step(s, 0, fz);
+                    if (q != GC_OK) return q;
+                }
+                if (s->p.timing) {  // read this launch's events before they are re-recorded
+                    gc_status q = read_ctrl(s);
+                    if (q != GC_OK) return q;
+                    const long long did = std::min<long long>(K, s->h_ctrl->step - before);
+                    for (long long k = 0; k < did; ++k) {
+                        float ms = 0.f;
+                        if (s->phys.coulomb) {
+                            GC_CUDA(cudaEventElapsedTime(&ms, s->ev_a[k], s->ev_b[k]));
+                            s->pair_ms += ms;
+                            s->pair_launches += 1;
+                        }
+                        GC_CUDA(cudaEventElapsedTime(&ms, s->ev_b[k], s->ev_c[k]));
+                        s->integ_ms += ms;
+                        GC_CUDA(cudaEventElapsedTime(&ms, s->ev_c[k], s->ev_d[k]));
+                        s->compact_ms += ms;
+                        s->timed_steps += 1;
+                    }
+                }
+                return GC_OK;
+            };
+            if (use_graph(s) && loops) {
+                // the device-side loop runs to the limit, to completion or (the
+                // unfused loop) to the hand-over, in one launch
+                GC_CUDA(cudaGraphLaunch(g, s->stream));
+                r = read_ctrl(s);
+                if (r != GC_OK) return r;
+            } else if (steps >= 0) {
+                // known step count: enqueue everything, synchronise once
+                for (long long k = 0; k < (want + K - 1) / K; ++k) {
                     r = launch_one();
                     if (r != GC_OK) return r;
                 }
                 r = read_ctrl(s);
                 if (r != GC_OK) return r;
-                if (s->h_ctrl->n_active <= 0 || s->h_ctrl->step >= limit) break;
-                if (s->h_ctrl->step == before) return GC_ERR_STATE;  // no progress: never spin
+            } else {
+                // until every carrier is collected: poll between batches of steps
+                const long long batch = std::max(1, 256 / K);
+                for (;;) {
+                    const long long before = s->h_ctrl->step;
+                    for (long long k = 0; k < batch; ++k) {
+                        r = launch_one();
+                        if (r != GC_OK) return r;
+                    }
+                    r = read_ctrl(s);
+                    if (r != GC_OK) return r;
+                    if (s->h_ctrl->n_active <= 0 || s->h_ctrl->step >= limit) break;
+                    if (s->h_ctrl->step == before) return GC_ERR_STATE;  // no progress: never spin
+                    if (!fz && s->fused_ok && s->h_ctrl->n_active <= kFusedMax) break;  // hand over
+                }
             }
+            if (fz || s->h_ctrl->n_active <= 0 || s->h_ctrl->step >= limit) break;
+            if (!(s->fused_ok && s->h_ctrl->n_active <= kFusedMax)) break;
         }
         r = set_limit(s, s->h_ctrl->step);  // closed until the next gc_run
         if (r != GC_OK) return r;
@@ -885,7 +992,8 @@ gc_status gc_get_stats(gc_sim *s, gc_stats *out) {
     out->integrate_kernel_ms = s->integ_ms;
     out->compact_kernel_ms = s->compact_ms;
     out->timed_steps = s->timed_steps;
-    out->device_loop = s->graph_loops ? 1 : 0;
+    out->device_loop = use_graph(s) && (!s->graph || s->graph_loops) && (!s->graph_small || s->small_loops);
+    out->fused_path = s->fused_ran ? 1 : 0;
     return GC_OK;
 }
 
@@ -951,6 +1059,8 @@ gc_status gc_restore_state(gc_sim *s, const gc_state *st) {
     GC_CUDA(cudaMemcpyAsync(d.ev_off[0], ioff.data(), (E + 1) * 4, cudaMemcpyHostToDevice, q));
     GC_CUDA(cudaMemsetAsync(d.ev_collected_now, 0, E * 4, q));
     GC_CUDA(cudaMemsetAsync(d.chunk_cnt, 0, (size_t)ceil_div((int)std::max<int64_t>(n, 1), kChunk) * 4, q));
+    if (d.tile_ticket)
+        GC_CUDA(cudaMemsetAsync(d.tile_ticket, 0, ((size_t)std::max<int64_t>(n, 1) / 8 + E + 1) * 4, q));
     GC_CUDA(cudaStreamSynchronize(q));
     Ctrl c{};
     c.step = st->step;
@@ -968,7 +1078,7 @@ gc_status gc_restore_state(gc_sim *s, const gc_state *st) {
         GC_CUDA(launch_integrate(d, f64, true, s->integ_grid, q));
         GC_CUDA(launch_compact(d, f64, s->integ_grid, q));
         GC_CUDA(launch_finalize(d, true, q));
-        if (d.tile_frames) GC_CUDA(launch_shadow(d, q));
+        if (d.tile_frames) GC_CUDA(launch_shadow(d, s->sm_count, q));
     }
     gc_status r = set_limit(s, st->step);
     if (r != GC_OK) return r;
@@ -1000,18 +1110,7 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
     Dev d{};
     d.phys = make_phys(p);
     const bool f64 = precision == GC_FP64;
-    std::vector<long long> sizes{n};
-    if (f64) {
-        d.shape.R = 1;
-        d.shape.small_n = 0;
-        d.shape.n_blocks = sms * std::max(1, pair_kernel_occupancy(GC_FP64, 1, 0, 0));
-        d.shape.jchunk = round_up(n, kTileJ);
-    } else {
-        d.shape.R = 4;
-        d.shape.small_n = kSmallEvent;
-        d.shape.n_blocks = sms * std::max(1, pair_kernel_occupancy(precision, 4, 0, 0));
-        d.shape.jchunk = choose_jchunk(sizes, 4, kSmallEvent, d.shape.n_blocks, 0);
-    }
+    d.shape = field_shape(precision, sms, n, 0);
     const long long S = (n + d.shape.jchunk - 1) / d.shape.jchunk;
     DevAllocs m;
     gc_status status = GC_OK;

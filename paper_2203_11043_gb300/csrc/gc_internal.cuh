@@ -30,6 +30,8 @@ constexpr int kChunk = 4096;        // slots per integrate/compact chunk
 constexpr int kChunkThreads = 1024; // threads per integrate/compact block
 constexpr int kPairThreads = 128;   // threads per pair-kernel block
 constexpr int kTileJ = 256;         // j positions staged in shared memory per tile
+constexpr int kTileJ64 = 64;        // FP64 form: granularity of its j-chunks
+constexpr int kFusedMax = 8192;     // fused small-workload step while at most this many holes are active
 constexpr float kSentinel = 1.0e15f; // padding position: its Eq. 6 term rounds to 0
 constexpr int kSmallEvent = 2048;    // FP32 forms: smaller events split j over 4 lanes and use
                                      // the event frame; larger ones one lane (and, with
@@ -49,7 +51,7 @@ struct Ctrl {
     unsigned long long carrier_steps;     // sum of active carriers over steps
     unsigned long long pair_interactions; // sum over steps of sum_e n_e^2
     int error;               // device-detected inconsistency (bit flags)
-    int pad;
+    int tiles_total;         // i-tiles of the next step (fused small-workload path)
 };
 
 // Physics and geometry, precomputed on the host from gc_params.
@@ -72,10 +74,11 @@ struct Phys {
 
 // Pair-kernel work decomposition, fixed at load time.
 struct PairShape {
-    int R;          // i carriers per thread (register blocking)
-    int jchunk;     // j-chunk length of a work item (multiple of kTileJ)
-    int small_n;    // events with fewer active carriers use 4 lanes per i-group
-    int n_blocks;   // persistent grid size
+    int R;           // i carriers per thread (register blocking; 1 in the FP64 form)
+    int jchunk;      // j-chunk length of a work item (multiple of kTileJ; of kTileJ64 in FP64)
+    int small_n;     // events with fewer active carriers use small_lanes lanes per i-group
+    int small_lanes; // lanes per i-group of small events: 4 (FP32 forms) or 16 (FP64 form)
+    int n_blocks;    // persistent grid size
 };
 
 // Device view of a simulation, passed by value to every kernel.
@@ -106,8 +109,14 @@ struct Dev {
     int *occ_pix;            // stored charge: occupied pixel indices, per event in index order
     int *occ_off;            // [E+1] capacity offsets of each event's occupied-pixel list
     int *occ_cnt;            // [E] occupied pixels this step
+    unsigned *occ_q;         // stored charge: exact count of each listed pixel at the step start
     float4 *occ_f4;          // stored charge, FP32 forms: (centre x, y relative to the event origin, count, 0)
     unsigned long long *off_image;
+    // fused small-workload path: per i-tile prefix over events [E+1], one
+    // ticket per i-tile (counts the j-chunk items done), one keep byte per slot
+    int *tile_base;
+    unsigned *tile_ticket;
+    unsigned char *keep8;
     Ctrl *ctrl;
     int n_total;
     int n_events;
@@ -124,7 +133,7 @@ struct Dev {
 constexpr int kFineUnit = 256;
 constexpr int kFineMaxChunks = 8;
 __host__ __device__ inline bool fine_units(int n_act) { return (n_act + kChunk - 1) / kChunk <= kFineMaxChunks; }
-__host__ __device__ inline int lanes_for(int n, int small_n) { return n < small_n ? 4 : 1; }
+__host__ __device__ inline int lanes_for(const PairShape &sh, int n) { return n < sh.small_n ? sh.small_lanes : 1; }
 __host__ __device__ inline int itile_for(int R, int lanes) { return R * kPairThreads / lanes; }
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 

@@ -2,9 +2,26 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
+#include "gcoreccd.h"
 #include "gc_internal.cuh"
 
 namespace gc {
+
+// Record the text of a failed CUDA call for gc_last_cuda_error and map it to
+// a status (GC_ERR_NO_DEVICE, GC_ERR_ALLOC or GC_ERR_CUDA).
+gc_status cuda_fail(cudaError_t e);
+
+// j-chunk length of the pair work items for events of the given sizes under
+// shape `sh` (R, small_n, small_lanes, n_blocks resident blocks), a multiple
+// of `gran` (user > 0 forces it, rounded up to a multiple of gran).
+int choose_jchunk(const std::vector<long long> &sizes, const PairShape &sh, int user, int gran);
+
+// Shape of the standalone Eq. 6 evaluation (gc_coulomb_field and its
+// allocation-free variant) of one event of n carriers; max_chunks > 0 caps
+// the number of j-chunks (the partial-sum capacity).
+PairShape field_shape(int precision, int sm_count, long long n, long long max_chunks);
 
 // Pair kernel (Eq. 6): precision 0 = FP64 form, 1 = FP32, 2 = FP32 + Kahan,
 // 3 = FP16x2; tile_frames != 0 selects the FP32 forms' tile-frame variant.
@@ -21,14 +38,23 @@ cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st);
 // FP32 forms with tile frames: the position shadow for the next step (tile
 // frames for large events, the event centroid otherwise) and the FP16x2
 // extents.  Without tile frames the compaction writes the shadow.
-cudaError_t launch_shadow(const Dev &d, cudaStream_t st);
+cudaError_t launch_shadow(const Dev &d, int sm_count, cudaStream_t st);
 // Stored charge (Sec. 1): the occupied pixels of each event's image, in
 // pixel-index order, as the field sources of the coming integrate.
 cudaError_t launch_occupied_pixels(const Dev &d, cudaStream_t st);
 // Device-side loop condition of a captured WHILE graph node: continue while
 // carriers are active, the step limit is not reached and the last pass made
 // progress (so the loop always ends).
-cudaError_t launch_loop_cond(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st);
+cudaError_t launch_loop_cond(const Dev &d, cudaGraphConditionalHandle h, int switch_below,
+                             cudaStream_t st);
+// Fused small-workload step (FP32 forms without Newton step or tile frames,
+// and the FP64 form; no stored charge): the pair kernel that also integrates
+// each i-tile as its last j-chunk completes, then one block that compacts and
+// does the bookkeeping.
+const void *fused_pair_kernel_ptr(int precision, int R);
+int fused_pair_occupancy(int precision, int R);
+cudaError_t launch_fused_pair(const Dev &d, int precision, int grid, cudaStream_t st);
+cudaError_t launch_small_tail(const Dev &d, bool fp64, cudaStream_t st);
 // Recompute the pair work items from the current active offsets (after the
 // pair-kernel shape changes).
 cudaError_t launch_build_items(const Dev &d, cudaStream_t st);

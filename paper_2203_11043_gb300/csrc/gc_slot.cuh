@@ -1,0 +1,240 @@
+// gc_slot.cuh -- the per-carrier part of one time step (Fig. 2), shared by
+// the integrate kernel and the fused small-workload pair kernel so that both
+// run the same arithmetic: Eq. 1 + Eq. 6 field, Eq. 2 mobility, drift,
+// Eqs. 3-4 diffusion from Philox-4x32-10 normals, the FP64 position update,
+// back-surface reflection, the z check and the pixel binning (Fig. 5).
+#pragma once
+#include "gc_internal.cuh"
+
+namespace gc {
+
+// ---- Eq. 2 mobility -------------------------------------------------------------
+__device__ __forceinline__ double mobility64(const Phys &ph, double E) {
+    return ph.mu0 / pow(1.0 + pow(E * ph.inv_Ec, ph.beta), ph.inv_beta);
+}
+__device__ __forceinline__ float mobility32(const Phys &ph, float E) {
+    const float t = exp2f((float)ph.beta * log2f(E * (float)ph.inv_Ec));
+    return (float)ph.mu0 * exp2f(-(float)ph.inv_beta * log2f(1.0f + t));
+}
+
+// ---- Box-Muller on the Philox bits (u_a in (0,1], u_b in [0,1)) ---------------------
+__device__ __forceinline__ void normals64(uint4 b, double n[3]) {
+    const double s = 2.3283064365386963e-10;  // 2^-32
+    const double r0 = sqrt(-2.0 * log(((double)b.x + 1.0) * s));
+    double sn, cs;
+    sincospi(2.0 * ((double)b.y * s), &sn, &cs);
+    n[0] = r0 * cs;
+    n[1] = r0 * sn;
+    const double r1 = sqrt(-2.0 * log(((double)b.z + 1.0) * s));
+    n[2] = r1 * cospi(2.0 * ((double)b.w * s));
+}
+__device__ __forceinline__ void normals32(uint4 b, float n[3]) {
+    const float s = 2.3283064365386963e-10f;  // 2^-32
+    const float r0 = sqrtf(-2.0f * logf(fmaf((float)b.x, s, s)));
+    float sn, cs;
+    sincospif(2.0f * ((float)b.y * s), &sn, &cs);
+    n[0] = r0 * cs;
+    n[1] = r0 * sn;
+    const float r1 = sqrtf(-2.0f * logf(fmaf((float)b.z, s, s)));
+    n[2] = r1 * cospif(2.0f * ((float)b.w * s));
+}
+
+// ---- block-wide exclusive scan (any block of up to 1024 threads, a multiple of 32) ------------
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *s_warp,
+                                                          long long &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        s_warp[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const long long ex = s_warp[warp] + incl - v;
+    total = s_warp[32];
+    __syncthreads();
+    return ex;
+}
+
+// ---- stored charge (Sec. 1) ----------------------------------------------------------
+// Field of the charge stored in event e's pixels at the carrier whose shadow
+// position (relative to the event origin o) is r: pixel (ix, iy) with count q
+// is q charges at (img_origin + (i + 1/2) p, stored_z), softened as in Eq. 6,
+// summed in pixel-index order.  Unscaled (multiply by K).
+template <typename T>
+__device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, T rz0, T &sx, T &sy,
+                                             T &sz) {
+    const Phys &ph = d.phys;
+    // pixel (0, 0) centre relative to the event origin
+    const T cx0 = (T)(d.img_origin[2 * e] + 0.5 * ph.pixel - d.ev_origin[3 * e]);
+    const T cy0 = (T)(d.img_origin[2 * e + 1] + 0.5 * ph.pixel - d.ev_origin[3 * e + 1]);
+    const T dz = rz0 - (T)(ph.stored_z - d.ev_origin[3 * e + 2]);
+    const T pix = (T)ph.pixel, eps2 = (T)ph.eps2;
+    const int *occ = d.occ_pix + d.occ_off[e];
+    const int cnt = d.occ_cnt[e];
+    sx = sy = sz = (T)0;
+    if constexpr (sizeof(T) == 4) {  // FP32 forms: precomputed centres, MUFU rsqrt
+        const float4 *c4 = d.occ_f4 + d.occ_off[e];
+        for (int k = 0; k < cnt; ++k) {
+            const float4 cq = c4[k];
+            const float dx = rx0 - cq.x, dy = ry0 - cq.y;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            const float iv = rsqrt_mufu(r2);
+            const float w = cq.z * iv * iv * iv;
+            sx = fmaf(dx, w, sx);
+            sy = fmaf(dy, w, sy);
+            sz = fmaf(dz, w, sz);
+        }
+        (void)occ;
+        (void)cx0;
+        (void)cy0;
+        (void)pix;
+    } else {
+        // the counts of the step-start snapshot: holes collected during this
+        // step's integrate add to the image concurrently and must not be seen
+        const unsigned *qs = d.occ_q + d.occ_off[e];
+        for (int k = 0; k < cnt; ++k) {
+            const int pidx = occ[k];
+            const int iy = pidx / ph.img_w, ix = pidx - iy * ph.img_w;
+            const T q = (T)qs[k];
+            const T dx = rx0 - (cx0 + (T)ix * pix), dy = ry0 - (cy0 + (T)iy * pix);
+            const T r2 = dx * dx + dy * dy + dz * dz + eps2;
+            const T w = q / (r2 * sqrt(r2));
+            sx += dx * w;
+            sy += dy * w;
+            sz += dz * w;
+        }
+    }
+}
+
+// ---- per-slot step -------------------------------------------------------------------
+// Returns true when the carrier stays active.
+// CG: read the per-chunk partial sums through L2 (ld.global.cg).  The fused
+// pair kernel integrates an i-tile in the same launch that wrote its partial
+// sums from other SMs, so this SM's L1 may hold a stale copy of their lines.
+template <bool F64, bool INIT, bool CG = false>
+__device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long long step) {
+    const Phys &ph = d.phys;
+    const int id = d.act[cur][p];
+    const int e = d.ev_of_id[id];
+    double x = d.px[id], y = d.py[id], z = d.pz[id];
+    if (INIT) {
+        if (ph.reflect && z > ph.thickness) {
+            z = 2.0 * ph.thickness - z;
+            d.pz[id] = z;
+        }
+    } else {
+        double ex = 0.0, ey = 0.0, ez = 0.0;
+        if (ph.coulomb) {  // Eq. 6: sum of the per-chunk partial sums, fixed order
+            const int *off = d.ev_off[cur];
+            const int n_e = off[e + 1] - off[e];
+            const int js = ceil_div(n_e, d.shape.jchunk);
+            const double *P = d.partial + p;
+            for (int jc = 0; jc < js; ++jc) {
+                if (CG) {
+                    ex += __ldcg(P);
+                    ey += __ldcg(P + d.part_stride);
+                    ez += __ldcg(P + 2 * d.part_stride);
+                } else {
+                    ex += P[0];
+                    ey += P[d.part_stride];
+                    ez += P[2 * d.part_stride];
+                }
+                P += 3 * d.part_stride;
+            }
+            ex *= ph.K;
+            ey *= ph.K;
+            ez *= ph.K;
+        }
+        if (ph.stored) {  // the charge already in the event's pixels (Sec. 1)
+            if (F64) {
+                const double4_32a r = d.sh64[p];
+                double sx, sy, sz;
+                stored_field<double>(d, e, r.x, r.y, r.z, sx, sy, sz);
+                ex += ph.K * sx;
+                ey += ph.K * sy;
+                ez += ph.K * sz;
+            } else {  // the FP32 shadow may be tile-relative: use the event frame here
+                const float rx = (float)(x - d.ev_origin[3 * e]), ry = (float)(y - d.ev_origin[3 * e + 1]),
+                            rz = (float)(z - d.ev_origin[3 * e + 2]);
+                float sx, sy, sz;
+                stored_field<float>(d, e, rx, ry, rz, sx, sy, sz);
+                ex += ph.K * (double)sx;
+                ey += ph.K * (double)sy;
+                ez += ph.K * (double)sz;
+            }
+        }
+        ez += ph.a1 * z - ph.a2;  // Eq. 1
+        double dx, dy, dz;
+        if (F64) {
+            const double E = sqrt(ex * ex + ey * ey + ez * ez);
+            const double mu = mobility64(ph, E);
+            const double vdt = 1e4 * mu * ph.dt;  // um per (V/cm)
+            dx = vdt * ex;
+            dy = vdt * ey;
+            dz = vdt * ez;
+            if (ph.diffusion) {
+                const double sigma = sqrt(2.0 * (1e8 * mu * ph.Vth) * ph.dt);
+                double n[3];
+                normals64(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
+                dx += sigma * n[0];
+                dy += sigma * n[1];
+                dz += sigma * n[2];
+            }
+        } else {
+            const float fx = (float)ex, fy = (float)ey, fz = (float)ez;
+            const float E = sqrtf(fx * fx + fy * fy + fz * fz);
+            const float mu = mobility32(ph, E);
+            const float vdt = 1e4f * mu * (float)ph.dt;
+            float ddx = vdt * fx, ddy = vdt * fy, ddz = vdt * fz;
+            if (ph.diffusion) {
+                const float sigma = sqrtf(2.0f * (1e8f * mu * (float)ph.Vth) * (float)ph.dt);
+                float n[3];
+                normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
+                ddx = fmaf(sigma, n[0], ddx);
+                ddy = fmaf(sigma, n[1], ddy);
+                ddz = fmaf(sigma, n[2], ddz);
+            }
+            dx = ddx;
+            dy = ddy;
+            dz = ddz;
+        }
+        x += dx;
+        y += dy;
+        z += dz;
+        if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
+        d.px[id] = x;
+        d.py[id] = y;
+        d.pz[id] = z;
+    }
+    if (z <= ph.z_well) {  // the z check: collected at this step
+        d.collect_step[id] = (int)step;
+        const int eu = d.ev_user[e];
+        const double fx = floor((x - d.img_origin[2 * e]) / ph.pixel);
+        const double fy = floor((y - d.img_origin[2 * e + 1]) / ph.pixel);
+        if (fx >= 0.0 && fx < (double)ph.img_w && fy >= 0.0 && fy < (double)ph.img_h) {
+            const long long pix = ((long long)eu * ph.img_h + (long long)fy) * ph.img_w + (long long)fx;
+            atomicAdd(&d.image[pix], 1u);
+        } else {
+            atomicAdd(&d.off_image[eu], 1ull);
+        }
+        atomicAdd(&d.ev_collected_now[e], 1);
+        return false;
+    }
+    return true;
+}
+
+}  // namespace gc

@@ -20,10 +20,10 @@ namespace gc {
 namespace {
 
 constexpr int kMaxN = GC_NOALLOC_MAX_CARRIERS;
-constexpr int kMaxChunks = 4;                  // j-chunks the partial area holds
-constexpr size_t kHeader = 4096;               // Ctrl, offsets, item bases, origin
+constexpr int kChunksAtMaxN = 8;               // j-chunks the partial area holds at n = kMaxN
+constexpr size_t kHeader = 4096;               // Ctrl, offsets, item bases, origin, FP16x2 extent
 constexpr size_t kShadowBytes = (size_t)kMaxN * 32;            // float4 or double4_32a
-constexpr size_t kPartialBytes = (size_t)kMaxChunks * 3 * kMaxN * 8;
+constexpr size_t kPartialBytes = (size_t)kChunksAtMaxN * 3 * kMaxN * 8;
 constexpr size_t kScratchBytes = kHeader + kShadowBytes + kPartialBytes;
 static_assert(sizeof(Ctrl) <= 256, "control block must fit its slot");
 
@@ -35,8 +35,8 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_dev[kMaxDevices] = {};  // device address of g_scratch, per device
 
-// Resets the control block and the single-event bookkeeping for one call;
-// the event origin is the first carrier's position.
+// Resets the control block, the single-event bookkeeping and the FP16x2
+// extent for one call; the event origin is the first carrier's position.
 __global__ void noalloc_setup_kernel(Dev d, const double *__restrict__ xyz, int n) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         Ctrl c{};
@@ -49,6 +49,7 @@ __global__ void noalloc_setup_kernel(Dev d, const double *__restrict__ xyz, int 
         d.ev_origin[0] = xyz[0];
         d.ev_origin[1] = xyz[1];
         d.ev_origin[2] = xyz[2];
+        if (d.ev_ext[0]) d.ev_ext[0][0] = 0u;  // FP16x2 form only
     }
 }
 
@@ -63,13 +64,16 @@ extern "C" gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, 
     if (n < 0 || n > kMaxN) return GC_ERR_PARAM;
     if (!(softening_um > 0) || !(softening_um < 1e300) || !(eps_si_rel > 0) || !(eps_si_rel < 1e300))
         return GC_ERR_PARAM;
-    if (precision < GC_FP64 || precision > GC_FP32_KAHAN) return GC_ERR_PARAM;
+    if (precision < GC_FP64 || precision > GC_FP16X2) return GC_ERR_PARAM;
     if (n > 0 && (!xyz_dev || !E_dev)) return GC_ERR_PARAM;
     int cnt = 0;
-    if (cudaGetDeviceCount(&cnt) != cudaSuccess || cnt == 0) return GC_ERR_NO_DEVICE;
+    cudaError_t e = cudaGetDeviceCount(&cnt);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cnt == 0) return GC_ERR_NO_DEVICE;
     if (n == 0) return GC_OK;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GC_ERR_CUDA;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kMaxDevices) return GC_ERR_PARAM;
 
     // Once per device, with that device current: the scratch's device address.
     void *base = nullptr;
@@ -77,13 +81,15 @@ extern "C" gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, 
         std::lock_guard<std::mutex> lock(g_mutex);
         if (!g_scratch_dev[dev]) {
             void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return GC_ERR_CUDA;
+            if ((e = cudaGetSymbolAddress(&p, g_scratch)) != cudaSuccess) return cuda_fail(e);
+            if (!p) return GC_ERR_CUDA;
             g_scratch_dev[dev] = p;
         }
         base = g_scratch_dev[dev];
     }
     int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GC_ERR_CUDA;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e);
 
     unsigned char *b = (unsigned char *)base;
     Dev d{};
@@ -91,6 +97,7 @@ extern "C" gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, 
     d.ev_off[0] = d.ev_off[1] = (int *)(b + 256);
     d.item_base = (int *)(b + 264);
     d.ev_origin = (double *)(b + 272);
+    if (precision == GC_FP16X2) d.ev_ext[0] = d.ev_ext[1] = (unsigned *)(b + 320);
     d.sh32 = (float4 *)(b + kHeader);
     d.sh64 = (double4_32a *)(b + kHeader);
     d.partial = (double *)(b + kHeader + kShadowBytes);
@@ -102,22 +109,17 @@ extern "C" gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, 
     d.phys.eps2 = softening_um * softening_um;
     d.phys.coulomb = 1;
     const bool f64 = precision == GC_FP64;
-    const int R = f64 ? 1 : 4;
-    d.shape.R = R;
-    d.shape.small_n = f64 ? 0 : kSmallEvent;
-    d.shape.n_blocks = sms * (pair_kernel_occupancy(precision, R, 0, 0) > 0
-                                  ? pair_kernel_occupancy(precision, R, 0, 0) : 1);
-    // at most kMaxChunks j-chunks, each a multiple of the shared-memory tile
-    const long long per = f64 ? n : (n + kMaxChunks - 1) / kMaxChunks;
-    d.shape.jchunk = (int)((per + kTileJ - 1) / kTileJ * kTileJ);
+    // the allocating entry point's shape, with j-chunks lengthened if the
+    // partial-sum area holds fewer of them
+    d.shape = field_shape(precision, sms, n, (long long)(kPartialBytes / (24 * (size_t)n)));
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     noalloc_setup_kernel<<<1, 32, 0, st>>>(d, xyz_dev, (int)n);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_field_prepare(d, xyz_dev, (int)n, f64, st);
     if (e == cudaSuccess) e = launch_build_items(d, st);
     if (e == cudaSuccess) e = launch_pair(d, precision, 0, st);
     if (e == cudaSuccess) e = launch_field_finish(d, (int)n, E_dev, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? GC_OK : GC_ERR_CUDA;
+    return e == cudaSuccess ? GC_OK : cuda_fail(e);
 }

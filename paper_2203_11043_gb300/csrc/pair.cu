@@ -1,371 +1,9 @@
-// pair.cu -- the Eq. 6 all-pairs softened Coulomb sum (Sec. 3.2, Fig. 3).
-//
-// E_i = K sum_{j in event(i), active} (r_i - r_j) / (|r_i - r_j|^2 + eps^2)^(3/2)
-//
-// The paper tiles positions through shared memory (GPU Gems 3 ch. 31,
-// Fig. 3: one thread per carrier, shPos tiles, __syncthreads between
-// tiles).  This file keeps the tiling idea but is shaped for sm_103a:
-//  * a persistent grid (one wave of resident blocks) pulls work items
-//    (event, i-tile, j-chunk) from an atomic counter; items are ordered by
-//    event, events by descending size (largest first), so thousands of
-//    uneven events share one launch and one big event splits into
-//    equal-cost items;
-//  * each thread keeps R i-carriers in registers, each duplicated as a
-//    packed FP32 pair {x_i, x_i}, and pairs it with two j's at a time: every
-//    step of the pair term runs as packed f32x2 instructions
-//    (sub/fma/mul .f32x2) with the reciprocal square root on MUFU;
-//  * j positions arrive by cp.async one tile ahead and are staged in shared
-//    memory as SoA tiles, so one 16-byte broadcast load per coordinate feeds
-//    four j's (two packed pairs) to every i of the thread;
-//  * per-tile FP32 sums are folded into Kahan-compensated running sums
-//    (FP32_KAHAN), and each item writes an FP64 partial per j-chunk; the
-//    integrate kernel adds the chunks in a fixed order (deterministic);
-//  * events smaller than `small_n` run 4 lanes per i-group that split the
-//    j range and combine with warp shuffles, so small events keep the
-//    block busy.
-#include "gc_internal.cuh"
+// pair.cu -- instantiation and launch of the Eq. 6 pair kernels of one time
+// step (templates in gc_pair.cuh).
+#include "gc_pair.cuh"
 #include "gc_launch.h"
 
 namespace gc {
-
-// ---------------------------------------------------------------------------
-// FP32 work item, packed over j: each thread owns R i-carriers, each held
-// duplicated as {x_i, x_i}; the shared tile is SoA (x[], y[], z[]) so one
-// 16-byte load per coordinate brings four consecutive j's as two packed pairs
-// {x_j, x_j+1}.  Each packed accumulator holds the even-j and odd-j sums of
-// one i; the Kahan state of the cross-tile sums stays in registers.  L lanes
-// share an i-group and split the j range.
-//
-// H16 (the FP16x2 form): coordinates are multiplied by the event's
-// power-of-two scale s (exact), the differences are rounded to f16x2 and
-// r^2 s^2 is formed with packed half FMAs; the reciprocal square root and the
-// accumulation stay FP32 and the sum is multiplied by s^2 at the end.
-//
-// Tile frames (TF; large events, one lane per i-group): the shadow of a hole
-// is relative to the FP64 origin of its 256-slot tile, held as an FP32 hi + lo
-// pair.  An item works in the frame I of its first i-tile: each i and, while
-// a j-tile is staged, each j is moved into I by adding (hi_t - hi_I) +
-// (lo_t - lo_I) for its own tile t.  The i's are shifted once per item (they
-// stay loop-invariant, as in the event frame), both sides use the same
-// expression, so a hole's self term stays exactly 0, and differences of close
-// holes are taken between small FP32 numbers.  The j-tile origins reach
-// shared memory (s_fr) by cp.async with the tile before.  s_fr is written by
-// other threads, so it is not a restrict pointer.
-template <int R, bool KAHAN, bool NEWTON, int L, bool H16, bool TF>
-__device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int n_e, int local,
-                                                 float scale, float *__restrict__ sx,
-                                                 float *__restrict__ sy, float *__restrict__ sz,
-                                                 float4 *s_fr, float4 *s_raw) {
-    constexpr int G = 32 / L;
-    constexpr int STRIDE = kPairThreads / L;
-    constexpr int IB = R * STRIDE;
-    // j positions per shared-memory tile (a multiple of the 256-slot frame
-    // tile): tile frames need one frame per staged tile; otherwise longer tiles
-    // amortise the barriers (4 lanes split a tile, so the 4-lane path takes 4
-    // tiles' worth).  Measured on 4096 X-ray events: +3.4 % for the 4-lane path.
-    constexpr int TJ = L == 1 ? (TF ? kTileJ : 2 * kTileJ) : 4 * kTileJ;
-    constexpr int PER = TJ / kPairThreads;
-    // 16-byte loads (4 j's) per coordinate per iteration: about 16 packed
-    // pair chains in flight per lane (R * JU * 2 = 16 on one lane; the 4-lane
-    // path measured best at 4 for R = 2, against 2 and 8)
-    constexpr int JU = L == 1 ? (R >= 8 ? 1 : 8 / R) : 4;
-    constexpr int STEP = 4 * JU * L;  // j's consumed per unrolled iteration by the L lanes
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane / L, ph = lane % L;
-    const int jchunk = d.shape.jchunk;
-    const int js = ceil_div(n_e, jchunk);
-    const int it = local / js, jc = local - it * js;
-    const int il0 = it * IB + warp * G + g;
-
-    f2 xi[R], yi[R], zi[R], ax[R], ay[R], az[R];
-    const f2 ZERO = pack2(0.f, 0.f);
-    f2 kreg[KAHAN ? 6 * R : 1];  // Kahan sums and compensations, {even, odd} j
-    float4 Ih = make_float4(0.f, 0.f, 0.f, 0.f), Il = Ih;  // tile frames: the item frame I
-    if (TF) {
-        Ih = d.frame_hi[e_start + it * IB];  // it * IB is a tile start
-        Il = d.frame_lo[e_start + it * IB];
-        if (tid < 2) s_fr[tid] = tid ? Il : Ih;
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        float4 a = make_float4(kSentinel, kSentinel, kSentinel, 0.f);
-        const int ia = il0 + r * STRIDE;
-        if (ia < n_e) {
-            a = d.sh32[e_start + ia];
-            if (TF) {  // into the item frame
-                const int t = e_start + (ia & ~(kTileJ - 1));
-                const float4 th = d.frame_hi[t], tl = d.frame_lo[t];
-                a.x = a.x + ((th.x - Ih.x) + (tl.x - Il.x));
-                a.y = a.y + ((th.y - Ih.y) + (tl.y - Il.y));
-                a.z = a.z + ((th.z - Ih.z) + (tl.z - Il.z));
-            }
-        }
-        if (H16) {
-            a.x *= scale;
-            a.y *= scale;
-            a.z *= scale;
-        }
-        xi[r] = pack2(a.x, a.x);
-        yi[r] = pack2(a.y, a.y);
-        zi[r] = pack2(a.z, a.z);
-        ax[r] = ay[r] = az[r] = ZERO;
-        if (KAHAN) {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) kreg[r * 6 + c] = ZERO;
-        }
-    }
-    const float eps2f = (float)d.phys.eps2 * (H16 ? scale * scale : 1.0f);
-    const f2 EPS2 = pack2(eps2f, eps2f);
-    const unsigned EPS2H = f2_to_h2(EPS2);
-
-    const int j0 = jc * jchunk;
-    const int j1 = min(n_e, j0 + jchunk);
-    float4 *s_fj = s_fr + 2;  // j-tile frames (hi, lo), double-buffered by tile parity
-    // The next j-tile goes by cp.async into this thread's own landing slots
-    // (s_raw[u * 128 + tid], zero-filled past j1); at the tile start each
-    // thread moves its own slots into the SoA tile, so s_raw needs no barrier.
-    auto fetch = [&](int jt) {
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int j = jt + u * kPairThreads + tid;
-            cp_async16_zfill(s_raw + u * kPairThreads + tid, d.sh32 + e_start + (j < j1 ? j : j0),
-                             j < j1 ? 16u : 0u);
-        }
-        if (TF && tid < 2)  // jt is a tile start (j-chunks are whole tiles)
-            cp_async16(s_fj + 2 * ((jt / TJ) & 1) + tid,
-                       (tid ? d.frame_lo : d.frame_hi) + e_start + jt);
-    };
-    fetch(j0);
-    for (int jt = j0; jt < j1; jt += TJ) {
-        cp_async_wait_all();  // this thread's slots of the tile (and the tile's frame) have landed
-        __syncthreads();      // the previous tile has been consumed
-        float ox = 0.f, oy = 0.f, oz = 0.f;
-        if (TF) {  // this j-tile's frame relative to the item frame
-            const int b = 2 * ((jt / TJ) & 1);
-            const float4 th = s_fj[b], tl = s_fj[b + 1], ih = s_fr[0], il = s_fr[1];
-            ox = (th.x - ih.x) + (tl.x - il.x);
-            oy = (th.y - ih.y) + (tl.y - il.y);
-            oz = (th.z - ih.z) + (tl.z - il.z);
-        }
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int k = u * kPairThreads + tid;
-            const float sc = H16 ? scale : 1.0f;  // exact (power of two)
-            float4 v = s_raw[k];
-            if (jt + k >= j1) v = make_float4(kSentinel, kSentinel, kSentinel, 0.f);
-            if (TF) {
-                sx[k] = (v.x + ox) * sc;
-                sy[k] = (v.y + oy) * sc;
-                sz[k] = (v.z + oz) * sc;
-            } else {
-                sx[k] = v.x * sc;
-                sy[k] = v.y * sc;
-                sz[k] = v.z * sc;
-            }
-        }
-        __syncthreads();
-        const int cnt = min(TJ, j1 - jt);
-        if (jt + TJ < j1) fetch(jt + TJ);  // overlaps the loads with this tile's work
-        const int kmax = (cnt + STEP - 1) / STEP * STEP;  // padded with sentinels
-        auto j_step = [&](const int k0) {  // 4 * JU j's per lane: two packed pairs per load
-#pragma unroll
-            for (int u = 0; u < JU; ++u) {
-                const int k = k0 + u * 4 * L;
-                const ulonglong2 X = *reinterpret_cast<const ulonglong2 *>(sx + k);
-                const ulonglong2 Y = *reinterpret_cast<const ulonglong2 *>(sy + k);
-                const ulonglong2 Z = *reinterpret_cast<const ulonglong2 *>(sz + k);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const f2 xj = h ? X.y : X.x, yj = h ? Y.y : Y.x, zj = h ? Z.y : Z.x;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const f2 dx = sub2(xi[r], xj);
-                        const f2 dy = sub2(yi[r], yj);
-                        const f2 dz = sub2(zi[r], zj);
-                        float ra, rb;
-                        f2 r2;
-                        if (H16) {
-                            const unsigned hx = f2_to_h2(dx), hy = f2_to_h2(dy), hz = f2_to_h2(dz);
-                            unsigned h = hfma2(hx, hx, EPS2H);
-                            h = hfma2(hy, hy, h);
-                            h = hfma2(hz, hz, h);
-                            h2_to_f(h, ra, rb);
-                            r2 = pack2(ra, rb);
-                        } else {
-                            r2 = fma2(dx, dx, EPS2);
-                            r2 = fma2(dy, dy, r2);
-                            r2 = fma2(dz, dz, r2);
-                            unpack2(r2, ra, rb);
-                        }
-                        f2 inv = pack2(rsqrt_mufu(ra), rsqrt_mufu(rb));
-                        if (NEWTON) {  // y <- y (3/2 - r2 y^2 / 2)
-                            const f2 nh = mul2(r2, pack2(-0.5f, -0.5f));
-                            const f2 t = fma2(nh, mul2(inv, inv), pack2(1.5f, 1.5f));
-                            inv = mul2(inv, t);
-                        }
-                        const f2 inv3 = mul2(mul2(inv, inv), inv);
-                        ax[r] = fma2(dx, inv3, ax[r]);
-                        ay[r] = fma2(dy, inv3, ay[r]);
-                        az[r] = fma2(dz, inv3, az[r]);
-                    }
-                }
-            }
-        };
-        if (TF) {  // measured: unrolling by 2 suits the tile-frame variant, not the other
-#pragma unroll 2
-            for (int k0 = 4 * ph; k0 < kmax; k0 += STEP) j_step(k0);
-        } else {
-            for (int k0 = 4 * ph; k0 < kmax; k0 += STEP) j_step(k0);
-        }
-        if (KAHAN) {  // fold this tile's sums into the compensated totals
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const f2 acc[3] = {ax[r], ay[r], az[r]};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const f2 s0 = kreg[r * 6 + 2 * c], c0 = kreg[r * 6 + 2 * c + 1];
-                    const f2 y = sub2(acc[c], c0), t = add2(s0, y);
-                    kreg[r * 6 + 2 * c + 1] = sub2(sub2(t, s0), y);
-                    kreg[r * 6 + 2 * c] = t;
-                }
-                ax[r] = ay[r] = az[r] = ZERO;
-            }
-        }
-    }
-
-    // Combine the even/odd halves and the L lanes of each i-group; write the FP64 partial.
-    double *P = d.partial + (long long)jc * 3 * d.part_stride;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        double v[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float lo, hi;
-            if (KAHAN) {
-                float clo, chi;
-                unpack2(kreg[r * 6 + 2 * c], lo, hi);
-                unpack2(kreg[r * 6 + 2 * c + 1], clo, chi);
-                v[c] = ((double)lo - (double)clo) + ((double)hi - (double)chi);
-                if (H16) v[c] *= (double)scale * (double)scale;
-            } else {
-                unpack2(c == 0 ? ax[r] : (c == 1 ? ay[r] : az[r]), lo, hi);
-                v[c] = (double)lo + (double)hi;
-            }
-#pragma unroll
-            for (int o = 1; o < L; o <<= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
-        }
-        const int il = il0 + r * STRIDE;
-        if (ph == 0 && il < n_e) {
-            const long long p = e_start + il;
-            P[p] = v[0];
-            P[d.part_stride + p] = v[1];
-            P[2 * d.part_stride + p] = v[2];
-        }
-    }
-}
-
-// Largest event e with item_base[e] <= item (events without items are skipped
-// because their base equals the next event's).
-__device__ __forceinline__ int event_of_item(const int *__restrict__ base, int n_events, int item) {
-    int lo = 0, hi = n_events;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (base[mid] <= item) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-// Min blocks = 1 lets ptxas keep many independent pair chains in registers
-// (R = 4: ~240 registers, 2 blocks per SM); measured faster than letting it
-// trade registers for occupancy.
-// TF: the tile-frame variant (used when some event is large enough for one
-// lane per i-group); its small events still run the event-frame path.
-template <int R, bool KAHAN, bool NEWTON, bool H16, bool TF>
-__global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
-    __shared__ __align__(16) float s_x[4 * kTileJ], s_y[4 * kTileJ], s_z[4 * kTileJ];
-    __shared__ float4 s_fr[TF ? 6 : 1];  // tile frames: the item frame, then two j-tile frames
-    __shared__ __align__(16) float4 s_raw[4 * kTileJ];  // cp.async landing slots of the next j-tile
-    __shared__ int s_item;
-    Ctrl *c = d.ctrl;
-    if (step_skipped(c)) return;
-    const int *off = d.ev_off[c->cur];
-    const unsigned *ext = H16 ? d.ev_ext[c->cur] : nullptr;
-    const int items = c->items_total;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(&c->work_counter, 1u);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= items) break;
-        const int e = event_of_item(d.item_base, d.n_events, item);
-        const int e_start = off[e], n_e = off[e + 1] - e_start;
-        const int local = item - d.item_base[e];
-        const float scale = H16 ? h2_scale(__uint_as_float(ext[e])) : 1.0f;
-        if (lanes_for(n_e, d.shape.small_n) == 1)
-            pair_item_fp32_j<R, KAHAN, NEWTON, 1, H16, TF>(d, e_start, n_e, local, scale, s_x, s_y,
-                                                           s_z, s_fr, s_raw);
-        else
-            pair_item_fp32_j<R, KAHAN, NEWTON, 4, H16, false>(d, e_start, n_e, local, scale, s_x, s_y,
-                                                              s_z, s_fr, s_raw);
-        __syncthreads();  // s_item and the tiles are reused by the next item
-    }
-}
-
-// ---------------------------------------------------------------------------
-// FP64 form: the plain per-carrier tiled sum in double precision (one
-// carrier per thread, shared-memory tiles, j in ascending order inside the
-// event), used as the reference form on the GPU.
-__global__ void __launch_bounds__(kPairThreads) pair_fp64_kernel(Dev d) {
-    constexpr int J = kPairThreads;
-    __shared__ double s_x[J], s_y[J], s_z[J];
-    __shared__ int s_item;
-    Ctrl *c = d.ctrl;
-    if (step_skipped(c)) return;
-    const int *off = d.ev_off[c->cur];
-    const int items = c->items_total;
-    const double eps2 = d.phys.eps2;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(&c->work_counter, 1u);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= items) break;
-        const int e = event_of_item(d.item_base, d.n_events, item);
-        const int e_start = off[e], n_e = off[e + 1] - e_start;
-        const int local = item - d.item_base[e];
-        const int js = ceil_div(n_e, d.shape.jchunk);
-        const int it = local / js, jc = local - it * js;
-        const int il = it * kPairThreads + threadIdx.x;
-        double4_32a me = make_double4_32a(0, 0, 0, 0);
-        if (il < n_e) me = d.sh64[e_start + il];
-        double ex = 0.0, ey = 0.0, ez = 0.0;
-        const int j0 = jc * d.shape.jchunk, j1 = min(n_e, j0 + d.shape.jchunk);
-        for (int jt = j0; jt < j1; jt += J) {
-            __syncthreads();
-            const int j = jt + threadIdx.x;
-            if (j < j1) {
-                const double4_32a q = d.sh64[e_start + j];
-                s_x[threadIdx.x] = q.x; s_y[threadIdx.x] = q.y; s_z[threadIdx.x] = q.z;
-            }
-            __syncthreads();
-            const int cnt = min(J, j1 - jt);
-            for (int k = 0; k < cnt; ++k) {
-                const double rx = me.x - s_x[k], ry = me.y - s_y[k], rz = me.z - s_z[k];
-                const double r2 = rx * rx + ry * ry + rz * rz + eps2;
-                const double inv = 1.0 / (r2 * sqrt(r2));
-                ex += rx * inv;
-                ey += ry * inv;
-                ez += rz * inv;
-            }
-        }
-        if (il < n_e) {
-            double *P = d.partial + (long long)jc * 3 * d.part_stride;
-            const long long p = e_start + il;
-            P[p] = ex;
-            P[d.part_stride + p] = ey;
-            P[2 * d.part_stride + p] = ez;
-        }
-        __syncthreads();
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Host-side launch table.
@@ -375,11 +13,11 @@ template <bool TF>
 static PairKernel fp32_kernel(int R, bool kahan, bool newton, bool h16) {
 #define GC_PICK(RR)                                                                        \
     if (R == RR) {                                                                         \
-        if (h16) return pair_fp32_kernel<RR, true, false, true, TF>; /* no Newton step */  \
-        if (kahan) return newton ? pair_fp32_kernel<RR, true, true, false, TF>             \
-                                 : pair_fp32_kernel<RR, true, false, false, TF>;           \
-        return newton ? pair_fp32_kernel<RR, false, true, false, TF>                       \
-                      : pair_fp32_kernel<RR, false, false, false, TF>;                     \
+        if (h16) return pair_fp32_kernel<RR, true, false, true, TF, false>; /* no Newton step */  \
+        if (kahan) return newton ? pair_fp32_kernel<RR, true, true, false, TF, false>             \
+                                 : pair_fp32_kernel<RR, true, false, false, TF, false>;           \
+        return newton ? pair_fp32_kernel<RR, false, true, false, TF, false>                       \
+                      : pair_fp32_kernel<RR, false, false, false, TF, false>;                     \
     }
     GC_PICK(2)
     GC_PICK(4)
@@ -389,7 +27,7 @@ static PairKernel fp32_kernel(int R, bool kahan, bool newton, bool h16) {
 }
 
 const void *pair_kernel_ptr(int precision, int R, int newton, int tile_frames) {
-    if (precision == 0) return (const void *)pair_fp64_kernel;
+    if (precision == 0) return (const void *)pair_fp64_kernel<false>;
     if (precision >= 1 && precision <= 3) {
         const bool kahan = precision >= 2, h16 = precision == 3;
         return tile_frames ? (const void *)fp32_kernel<true>(R, kahan, newton != 0, h16)

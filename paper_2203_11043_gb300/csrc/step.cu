@@ -16,39 +16,9 @@
 // captured graph), so nothing here can spin.
 #include "gc_internal.cuh"
 #include "gc_launch.h"
+#include "gc_slot.cuh"
 
 namespace gc {
-
-// ---- Eq. 2 mobility -------------------------------------------------------------
-__device__ __forceinline__ double mobility64(const Phys &ph, double E) {
-    return ph.mu0 / pow(1.0 + pow(E * ph.inv_Ec, ph.beta), ph.inv_beta);
-}
-__device__ __forceinline__ float mobility32(const Phys &ph, float E) {
-    const float t = exp2f((float)ph.beta * log2f(E * (float)ph.inv_Ec));
-    return (float)ph.mu0 * exp2f(-(float)ph.inv_beta * log2f(1.0f + t));
-}
-
-// ---- Box-Muller on the Philox bits (u_a in (0,1], u_b in [0,1)) ---------------------
-__device__ __forceinline__ void normals64(uint4 b, double n[3]) {
-    const double s = 2.3283064365386963e-10;  // 2^-32
-    const double r0 = sqrt(-2.0 * log(((double)b.x + 1.0) * s));
-    double sn, cs;
-    sincospi(2.0 * ((double)b.y * s), &sn, &cs);
-    n[0] = r0 * cs;
-    n[1] = r0 * sn;
-    const double r1 = sqrt(-2.0 * log(((double)b.z + 1.0) * s));
-    n[2] = r1 * cospi(2.0 * ((double)b.w * s));
-}
-__device__ __forceinline__ void normals32(uint4 b, float n[3]) {
-    const float s = 2.3283064365386963e-10f;  // 2^-32
-    const float r0 = sqrtf(-2.0f * logf(fmaf((float)b.x, s, s)));
-    float sn, cs;
-    sincospif(2.0f * ((float)b.y * s), &sn, &cs);
-    n[0] = r0 * cs;
-    n[1] = r0 * sn;
-    const float r1 = sqrtf(-2.0f * logf(fmaf((float)b.z, s, s)));
-    n[2] = r1 * cospif(2.0f * ((float)b.w * s));
-}
 
 // ---- FP32 position shadow with tile frames -------------------------------------------------------
 // Runs after finalize when tile frames are on (the new active list and event
@@ -115,87 +85,6 @@ __global__ void __launch_bounds__(256) shadow_kernel(Dev d) {
     }
 }
 
-// ---- block-wide exclusive scan (1024 threads) ------------------------------------------------
-__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *s_warp,
-                                                          long long &total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        long long w = s_warp[lane];
-        long long wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
-        }
-        s_warp[lane] = wi - w;  // exclusive prefix of warp totals
-        if (lane == 31) s_warp[32] = wi;
-    }
-    __syncthreads();
-    const long long ex = s_warp[warp] + incl - v;
-    total = s_warp[32];
-    __syncthreads();
-    return ex;
-}
-
-// ---- stored charge (Sec. 1) ----------------------------------------------------------
-// Field of the charge stored in event e's pixels at the carrier whose shadow
-// position (relative to the event origin o) is r: pixel (ix, iy) with count q
-// is q charges at (img_origin + (i + 1/2) p, stored_z), softened as in Eq. 6,
-// summed in pixel-index order.  Unscaled (multiply by K).
-template <typename T>
-__device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, T rz0, T &sx, T &sy,
-                                             T &sz) {
-    const Phys &ph = d.phys;
-    const int eu = d.ev_user[e];
-    const unsigned *img = d.image + (long long)eu * ph.img_h * ph.img_w;
-    // pixel (0, 0) centre relative to the event origin
-    const T cx0 = (T)(d.img_origin[2 * e] + 0.5 * ph.pixel - d.ev_origin[3 * e]);
-    const T cy0 = (T)(d.img_origin[2 * e + 1] + 0.5 * ph.pixel - d.ev_origin[3 * e + 1]);
-    const T dz = rz0 - (T)(ph.stored_z - d.ev_origin[3 * e + 2]);
-    const T pix = (T)ph.pixel, eps2 = (T)ph.eps2;
-    const int *occ = d.occ_pix + d.occ_off[e];
-    const int cnt = d.occ_cnt[e];
-    sx = sy = sz = (T)0;
-    if constexpr (sizeof(T) == 4) {  // FP32 forms: precomputed centres, MUFU rsqrt
-        const float4 *c4 = d.occ_f4 + d.occ_off[e];
-        for (int k = 0; k < cnt; ++k) {
-            const float4 cq = c4[k];
-            const float dx = rx0 - cq.x, dy = ry0 - cq.y;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-            const float iv = rsqrt_mufu(r2);
-            const float w = cq.z * iv * iv * iv;
-            sx = fmaf(dx, w, sx);
-            sy = fmaf(dy, w, sy);
-            sz = fmaf(dz, w, sz);
-        }
-        (void)occ;
-        (void)img;
-        (void)cx0;
-        (void)cy0;
-        (void)pix;
-    } else {
-        for (int k = 0; k < cnt; ++k) {
-            const int pidx = occ[k];
-            const int iy = pidx / ph.img_w, ix = pidx - iy * ph.img_w;
-            const T q = (T)img[pidx];
-            const T dx = rx0 - (cx0 + (T)ix * pix), dy = ry0 - (cy0 + (T)iy * pix);
-            const T r2 = dx * dx + dy * dy + dz * dz + eps2;
-            const T w = q / (r2 * sqrt(r2));
-            sx += dx * w;
-            sy += dy * w;
-            sz += dz * w;
-        }
-    }
-}
-
 // One block per event: the occupied pixels of its image in index order, for
 // the stored-charge field of this step.  Each thread takes 8 consecutive
 // pixels of a 8192-pixel span; one block-wide exclusive scan of the per-thread
@@ -227,6 +116,7 @@ __global__ void __launch_bounds__(kChunkThreads) occupied_pixels_kernel(Dev d) {
                     if (k_out < cap) {
                         const int pidx = first + k;
                         out[k_out] = pidx;
+                        d.occ_q[d.occ_off[e] + k_out] = img[pidx];
                         const int iy = pidx / d.phys.img_w, ix = pidx - iy * d.phys.img_w;
                         d.occ_f4[d.occ_off[e] + k_out] = make_float4(
                             (float)(d.img_origin[2 * e] + (ix + 0.5) * d.phys.pixel - d.ev_origin[3 * e]),
@@ -240,114 +130,6 @@ __global__ void __launch_bounds__(kChunkThreads) occupied_pixels_kernel(Dev d) {
         if (threadIdx.x == 0) d.occ_cnt[e] = (int)(base < cap ? base : (long long)cap);
         __syncthreads();
     }
-}
-
-// ---- per-slot step -------------------------------------------------------------------
-// Returns true when the carrier stays active.
-template <bool F64, bool INIT>
-__device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long long step) {
-    const Phys &ph = d.phys;
-    const int id = d.act[cur][p];
-    const int e = d.ev_of_id[id];
-    double x = d.px[id], y = d.py[id], z = d.pz[id];
-    if (INIT) {
-        if (ph.reflect && z > ph.thickness) {
-            z = 2.0 * ph.thickness - z;
-            d.pz[id] = z;
-        }
-    } else {
-        double ex = 0.0, ey = 0.0, ez = 0.0;
-        if (ph.coulomb) {  // Eq. 6: sum of the per-chunk partial sums, fixed order
-            const int *off = d.ev_off[cur];
-            const int n_e = off[e + 1] - off[e];
-            const int js = ceil_div(n_e, d.shape.jchunk);
-            const double *P = d.partial + p;
-            for (int jc = 0; jc < js; ++jc) {
-                ex += P[0];
-                ey += P[d.part_stride];
-                ez += P[2 * d.part_stride];
-                P += 3 * d.part_stride;
-            }
-            ex *= ph.K;
-            ey *= ph.K;
-            ez *= ph.K;
-        }
-        if (ph.stored) {  // the charge already in the event's pixels (Sec. 1)
-            if (F64) {
-                const double4_32a r = d.sh64[p];
-                double sx, sy, sz;
-                stored_field<double>(d, e, r.x, r.y, r.z, sx, sy, sz);
-                ex += ph.K * sx;
-                ey += ph.K * sy;
-                ez += ph.K * sz;
-            } else {  // the FP32 shadow may be tile-relative: use the event frame here
-                const float rx = (float)(x - d.ev_origin[3 * e]), ry = (float)(y - d.ev_origin[3 * e + 1]),
-                            rz = (float)(z - d.ev_origin[3 * e + 2]);
-                float sx, sy, sz;
-                stored_field<float>(d, e, rx, ry, rz, sx, sy, sz);
-                ex += ph.K * (double)sx;
-                ey += ph.K * (double)sy;
-                ez += ph.K * (double)sz;
-            }
-        }
-        ez += ph.a1 * z - ph.a2;  // Eq. 1
-        double dx, dy, dz;
-        if (F64) {
-            const double E = sqrt(ex * ex + ey * ey + ez * ez);
-            const double mu = mobility64(ph, E);
-            const double vdt = 1e4 * mu * ph.dt;  // um per (V/cm)
-            dx = vdt * ex;
-            dy = vdt * ey;
-            dz = vdt * ez;
-            if (ph.diffusion) {
-                const double sigma = sqrt(2.0 * (1e8 * mu * ph.Vth) * ph.dt);
-                double n[3];
-                normals64(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
-                dx += sigma * n[0];
-                dy += sigma * n[1];
-                dz += sigma * n[2];
-            }
-        } else {
-            const float fx = (float)ex, fy = (float)ey, fz = (float)ez;
-            const float E = sqrtf(fx * fx + fy * fy + fz * fz);
-            const float mu = mobility32(ph, E);
-            const float vdt = 1e4f * mu * (float)ph.dt;
-            float ddx = vdt * fx, ddy = vdt * fy, ddz = vdt * fz;
-            if (ph.diffusion) {
-                const float sigma = sqrtf(2.0f * (1e8f * mu * (float)ph.Vth) * (float)ph.dt);
-                float n[3];
-                normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
-                ddx = fmaf(sigma, n[0], ddx);
-                ddy = fmaf(sigma, n[1], ddy);
-                ddz = fmaf(sigma, n[2], ddz);
-            }
-            dx = ddx;
-            dy = ddy;
-            dz = ddz;
-        }
-        x += dx;
-        y += dy;
-        z += dz;
-        if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
-        d.px[id] = x;
-        d.py[id] = y;
-        d.pz[id] = z;
-    }
-    if (z <= ph.z_well) {  // the z check: collected at this step
-        d.collect_step[id] = (int)step;
-        const int eu = d.ev_user[e];
-        const double fx = floor((x - d.img_origin[2 * e]) / ph.pixel);
-        const double fy = floor((y - d.img_origin[2 * e + 1]) / ph.pixel);
-        if (fx >= 0.0 && fx < (double)ph.img_w && fy >= 0.0 && fy < (double)ph.img_h) {
-            const long long pix = ((long long)eu * ph.img_h + (long long)fy) * ph.img_w + (long long)fx;
-            atomicAdd(&d.image[pix], 1u);
-        } else {
-            atomicAdd(&d.off_image[eu], 1ull);
-        }
-        atomicAdd(&d.ev_collected_now[e], 1);
-        return false;
-    }
-    return true;
 }
 
 template <bool F64, bool INIT>
@@ -498,21 +280,27 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
 
 __device__ __forceinline__ int items_for(const Dev &d, int n) {
     if (n <= 0 || !d.phys.coulomb) return 0;
-    const int L = lanes_for(n, d.shape.small_n);
+    const int L = lanes_for(d.shape, n);
     return ceil_div(n, itile_for(d.shape.R, L)) * ceil_div(n, d.shape.jchunk);
 }
+__device__ __forceinline__ int tiles_for(const Dev &d, int n) {
+    if (n <= 0 || !d.phys.coulomb) return 0;
+    return ceil_div(n, itile_for(d.shape.R, lanes_for(d.shape, n)));
+}
 
+// One block (any multiple of 32 threads): per-event active counts after this
+// step's collections, the new event offsets, the pair work items and i-tiles
+// of the next step (prefix over events), the step and throughput counters,
+// and the flip of the double-buffered lists.
 template <bool INIT>
-__global__ void __launch_bounds__(kChunkThreads) finalize_kernel(Dev d) {
-    __shared__ long long s_warp[33];
+__device__ __forceinline__ void finalize_block(const Dev &d, long long *s_warp) {
     Ctrl *c = d.ctrl;
-    if (step_skipped(c)) return;
     const int cur = c->cur;
     const int *off = d.ev_off[cur];
     int *noff = d.ev_off[cur ^ 1];
-    long long carry_n = 0, carry_items = 0;
+    long long carry_n = 0, carry_items = 0, carry_tiles = 0;
     unsigned long long pairs = 0, cs = 0;
-    for (int base = 0; base < d.n_events; base += kChunkThreads) {
+    for (int base = 0; base < d.n_events; base += blockDim.x) {
         const int e = base + threadIdx.x;
         int n_old = 0, n_new = 0;
         if (e < d.n_events) {
@@ -522,31 +310,35 @@ __global__ void __launch_bounds__(kChunkThreads) finalize_kernel(Dev d) {
         }
         pairs += (unsigned long long)n_old * (unsigned long long)n_old;
         cs += (unsigned long long)n_old;
-        long long tn, ti;
+        long long tn, ti, tt = 0;
         const long long exn = block_exclusive_scan(n_new, s_warp, tn);
         const long long exi = block_exclusive_scan(items_for(d, n_new), s_warp, ti);
+        long long ext_ = 0;
+        if (d.tile_base) ext_ = block_exclusive_scan(tiles_for(d, n_new), s_warp, tt);
         if (e < d.n_events) {
             noff[e] = (int)(carry_n + exn);
             d.item_base[e] = (int)(carry_items + exi);
+            if (d.tile_base) d.tile_base[e] = (int)(carry_tiles + ext_);
         }
         carry_n += tn;
         carry_items += ti;
+        carry_tiles += tt;
     }
     // reduce the counters
-    long long dummy;
-    const long long tot_pairs_ex = block_exclusive_scan((long long)pairs, s_warp, dummy);
-    const long long tot_pairs = dummy;
-    const long long tot_cs_ex = block_exclusive_scan((long long)cs, s_warp, dummy);
-    const long long tot_cs = dummy;
-    (void)tot_pairs_ex;
-    (void)tot_cs_ex;
+    long long tot_pairs, tot_cs;
+    (void)block_exclusive_scan((long long)pairs, s_warp, tot_pairs);
+    (void)block_exclusive_scan((long long)cs, s_warp, tot_cs);
     // the next integrate accumulates its chunk counts atomically: zero them
-    if (fine_units((int)carry_n) && threadIdx.x < ceil_div((int)carry_n, kChunk)) d.chunk_cnt[threadIdx.x] = 0;
+    const int nch = ceil_div((int)carry_n, kChunk);
+    if (fine_units((int)carry_n))
+        for (int k = threadIdx.x; k < nch; k += blockDim.x) d.chunk_cnt[k] = 0;
     if (threadIdx.x == 0) {
         noff[d.n_events] = (int)carry_n;
         d.item_base[d.n_events] = (int)carry_items;
+        if (d.tile_base) d.tile_base[d.n_events] = (int)carry_tiles;
         c->n_active = (int)carry_n;
         c->items_total = (int)carry_items;
+        c->tiles_total = (int)carry_tiles;
         c->work_counter = 0u;
         c->cur = cur ^ 1;
         if (!INIT) {
@@ -557,10 +349,68 @@ __global__ void __launch_bounds__(kChunkThreads) finalize_kernel(Dev d) {
     }
 }
 
-__global__ void loop_cond_kernel(Dev d, cudaGraphConditionalHandle h) {
+template <bool INIT>
+__global__ void __launch_bounds__(kChunkThreads) finalize_kernel(Dev d) {
+    __shared__ long long s_warp[33];
+    if (step_skipped(d.ctrl)) return;
+    finalize_block<INIT>(d, s_warp);
+}
+
+// Fused small-workload path, after the fused pair kernel has integrated every
+// i-tile: one block compacts the active list from the keep bytes (stable,
+// thread t owning a contiguous run of slots), writes the next step's shadow
+// (and FP16x2 extents) exactly as compact_kernel does, then runs the
+// bookkeeping of finalize_kernel.
+template <bool F64>
+__global__ void __launch_bounds__(kChunkThreads) small_tail_kernel(Dev d) {
+    __shared__ long long s_warp[33];
+    Ctrl *c = d.ctrl;
+    if (step_skipped(c)) return;
+    const int cur = c->cur;
+    const int n_act = c->n_active;
+    const int *src = d.act[cur];
+    int *dst = d.act[cur ^ 1];
+    unsigned *ext = (!F64 && d.ev_ext[0]) ? d.ev_ext[cur ^ 1] : nullptr;
+    if (ext) {
+        for (int e = threadIdx.x; e < d.n_events; e += blockDim.x) ext[e] = 0u;
+        __syncthreads();
+    }
+    const int per = ceil_div(n_act, (int)blockDim.x);
+    const int p0 = min(n_act, (int)threadIdx.x * per), p1 = min(n_act, p0 + per);
+    int kept = 0;
+    for (int p = p0; p < p1; ++p) kept += d.keep8[p];
+    long long total;
+    int q = (int)block_exclusive_scan(kept, s_warp, total);
+#pragma unroll 4
+    for (int p = p0; p < p1; ++p) {
+        if (!d.keep8[p]) continue;
+        const int id = src[p];
+        dst[q] = id;
+        const int e = d.ev_of_id[id];
+        const double ox = d.ev_origin[3 * e], oy = d.ev_origin[3 * e + 1], oz = d.ev_origin[3 * e + 2];
+        if (F64) {
+            d.sh64[q] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
+        } else {
+            const float4 v = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
+                                         (float)(d.pz[id] - oz), 1.0f);
+            d.sh32[q] = v;
+            if (ext) atomicMax(&ext[e], __float_as_uint(fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)))));
+        }
+        ++q;
+    }
+    __syncthreads();
+    finalize_block<false>(d, s_warp);
+}
+
+// Device-side loop condition: continue while holes are active, the step limit
+// is not reached, the last pass advanced the step counter and (when a second,
+// fused small-workload graph takes over below it) more than switch_below
+// holes are active.
+__global__ void loop_cond_kernel(Dev d, cudaGraphConditionalHandle h, int switch_below) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     Ctrl *c = d.ctrl;
-    const bool go = c->n_active > 0 && c->step < c->step_limit && c->step != c->loop_last;
+    const bool go = c->n_active > switch_below && c->n_active > 0 && c->step < c->step_limit &&
+                    c->step != c->loop_last;
     c->loop_last = c->step;
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
@@ -570,18 +420,26 @@ __global__ void __launch_bounds__(kChunkThreads) build_items_kernel(Dev d) {
     __shared__ long long s_warp[33];
     Ctrl *c = d.ctrl;
     const int *off = d.ev_off[c->cur];
-    long long carry = 0;
+    long long carry = 0, carry_t = 0;
     for (int base = 0; base < d.n_events; base += kChunkThreads) {
         const int e = base + threadIdx.x;
         const int n = e < d.n_events ? off[e + 1] - off[e] : 0;
-        long long t;
+        long long t, tt = 0;
         const long long ex = block_exclusive_scan(items_for(d, n), s_warp, t);
-        if (e < d.n_events) d.item_base[e] = (int)(carry + ex);
+        long long ext_ = 0;
+        if (d.tile_base) ext_ = block_exclusive_scan(tiles_for(d, n), s_warp, tt);
+        if (e < d.n_events) {
+            d.item_base[e] = (int)(carry + ex);
+            if (d.tile_base) d.tile_base[e] = (int)(carry_t + ext_);
+        }
         carry += t;
+        carry_t += tt;
     }
     if (threadIdx.x == 0) {
         d.item_base[d.n_events] = (int)carry;
+        if (d.tile_base) d.tile_base[d.n_events] = (int)carry_t;
         c->items_total = (int)carry;
+        c->tiles_total = (int)carry_t;
         c->work_counter = 0u;
     }
 }
@@ -651,13 +509,20 @@ cudaError_t launch_finalize(const Dev &d, bool init, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_loop_cond(const Dev &d, cudaGraphConditionalHandle h, cudaStream_t st) {
-    loop_cond_kernel<<<1, 32, 0, st>>>(d, h);
+cudaError_t launch_loop_cond(const Dev &d, cudaGraphConditionalHandle h, int switch_below,
+                             cudaStream_t st) {
+    loop_cond_kernel<<<1, 32, 0, st>>>(d, h, switch_below);
     return cudaGetLastError();
 }
 
-cudaError_t launch_shadow(const Dev &d, cudaStream_t st) {
-    const int grid = max(1, min(ceil_div(d.n_total, 256), 8 * 152));
+cudaError_t launch_small_tail(const Dev &d, bool fp64, cudaStream_t st) {
+    if (fp64) small_tail_kernel<true><<<1, kChunkThreads, 0, st>>>(d);
+    else small_tail_kernel<false><<<1, kChunkThreads, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow(const Dev &d, int sm_count, cudaStream_t st) {
+    const int grid = max(1, min(ceil_div(d.n_total, 256), 8 * max(sm_count, 1)));
     shadow_kernel<<<grid, 256, 0, st>>>(d);
     return cudaGetLastError();
 }

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-GC_ABI_VERSION = 1
+GC_ABI_VERSION = 2
 GC_OK, GC_INCOMPLETE = 0, 1
 GC_ERR_PARAM, GC_ERR_ALLOC, GC_ERR_CUDA, GC_ERR_STATE = -1, -2, -3, -4
 GC_ERR_DEVICE_TIMEOUT, GC_ERR_NO_DEVICE = -5, -6
@@ -57,6 +57,8 @@ class GcParams(ctypes.Structure):
         ("stored_charge", ctypes.c_int32),
         ("tile_frames", ctypes.c_int32),
         ("stored_z_um", ctypes.c_double),
+        ("fuse_small", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -77,7 +79,7 @@ class GcStats(ctypes.Structure):
         ("compact_kernel_ms", ctypes.c_double),
         ("timed_steps", ctypes.c_int64),
         ("device_loop", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("fused_path", ctypes.c_int32),
     ]
 
 

@@ -465,3 +465,75 @@ def test_stored_charge_fp32_statistics(gc):
         assert res["positions"][:, c].std() == pytest.approx(ref.positions()[:, c].std(), rel=5e-3)
     l1 = np.abs(res["image"].astype(np.int64) - ref.image.astype(np.int64)).sum()
     assert l1 <= 0.01 * wl.n
+
+
+def dense_near_well_cloud():
+    """3,000 holes, sigma 1 um, centred 3.5 um above the wells (z from about 0.5
+    to 6.5 um), on 1 um pixels: within a few steps hundreds of holes are
+    collected per step, most of them into pixels that already hold charge."""
+    wl = I.single_cloud(n=3000, sigma_um=1.0, z0_um=3.5, seed=41, img=16)
+    return I.Workload(wl.name, wl.xyz, wl.ev_off, wl.seeds, np.array([[-8.0, -8.0]]), 16, 16)
+
+
+def test_stored_charge_fp64_dense_near_wells(gc):
+    """The stored-charge field uses the image at the start of the step (the
+    oracle's synchronous reading of Sec. 1): holes collected during a step
+    must not act on the other holes of the same step.  With many holes landing
+    per step in already occupied 1 um pixels, the FP64 form must reproduce the
+    oracle exactly (collection steps, images), be identical with and without
+    graphs, and be identical from run to run."""
+    wl = dense_near_well_cloud()
+    kw = dict(pixel_um=1.0, stored_charge=1, stored_z_um=-0.2)
+    ref = run_oracle(wl, **kw)
+    steps_hist = np.bincount(ref.collect_step[ref.collect_step > 0])
+    assert steps_hist.max() >= 200  # many collections per step: the case a live read gets wrong
+    outs = []
+    for gs in (0, 8, 8):
+        res = run_gpu(gc, wl, 0, graph_steps=gs, **kw)
+        assert_fp64_parity(res, ref, wl)
+        outs.append(res)
+    for o in outs[1:]:
+        assert np.array_equal(o["positions"], outs[0]["positions"])
+        assert np.array_equal(o["collect_step"], outs[0]["collect_step"])
+        assert np.array_equal(o["image"], outs[0]["image"])
+
+
+# ---- fused small-workload step --------------------------------------------------------------------
+
+def assert_same_run(a, b):
+    assert a["steps"] == b["steps"] and a["status"] == b["status"]
+    assert np.array_equal(a["positions"], b["positions"])
+    assert np.array_equal(a["collect_step"], b["collect_step"])
+    assert np.array_equal(a["image"], b["image"])
+    assert np.array_equal(a["n_offimage"], b["n_offimage"])
+    assert a["stats"]["pair_interactions"] == b["stats"]["pair_interactions"]
+    assert a["stats"]["carrier_steps"] == b["stats"]["carrier_steps"]
+
+
+@pytest.mark.parametrize("precision", [0, 2, 3])
+def test_fused_small_step_equals_four_launch_step(gc, precision):
+    """While at most 8192 holes are active a step is two launches (pair kernel
+    that integrates each i-tile when its last j-chunk is summed, then one
+    compaction block).  It runs the same items, partial sums and per-carrier
+    arithmetic as the four-launch step, so the results are the same bits:
+    the 5.9 keV cloud and the ragged batch, with graphs and eagerly."""
+    for wl, kw in ((I.xray_5p9kev(), {}), (ragged_batch(), dict(pixel_um=1.0))):
+        outs = []
+        for fuse, gs in ((0, 32), (1, 32), (1, 0)):
+            res = run_gpu(gc, wl, precision, fuse_small=fuse, graph_steps=gs, **kw)
+            assert res["stats"]["fused_path"] == fuse
+            outs.append(res)
+        for o in outs[1:]:
+            assert_same_run(o, outs[0])
+
+
+def test_fused_takes_over_below_its_limit(gc):
+    """A 12,000-hole cloud starts on the four-launch step and hands over to the
+    fused one once at most 8192 holes are active; the whole run is the same
+    bits as a run on the four-launch step throughout."""
+    wl = I.single_cloud(n=12000, sigma_um=0.6, z0_um=20.0, seed=44, img=32)
+    a = run_gpu(gc, wl, 2, fuse_small=0)
+    b = run_gpu(gc, wl, 2, fuse_small=1)
+    assert a["stats"]["fused_path"] == 0 and b["stats"]["fused_path"] == 1
+    assert_same_run(a, b)
+    assert b["status"] == 0 and b["stats"]["n_active"] == 0
