@@ -92,11 +92,14 @@ typedef struct {
                               pairs keep ~2^-24 of their tile's extent rather than of the event's;
                               costs a few percent of pair-kernel throughput; 0 = event frame */
     double stored_z_um;    /* depth of the stored-charge points */
-    int32_t fuse_small;    /* 1: while at most 8192 holes are active, each step is two launches (a
-                              pair kernel that also integrates every i-tile once its last j-chunk
-                              is summed, then one block that compacts); same results as the
-                              four-launch step.  Not used with newton, tile frames, stored charge
-                              or timing */
+    int32_t fuse_small;    /* while at most 8192 holes are active: 0 = the four-launch step
+                              throughout; 2 = each step two launches (a pair kernel that also
+                              integrates every i-tile once its last j-chunk is summed, then one
+                              block that compacts); 1 (default) = as 2, except that one event
+                              (FP64, FP32 or FP32 + Kahan) runs all its remaining steps in one
+                              cooperative launch with one grid barrier per step.  All give the
+                              same results as the four-launch step.  Not used with newton, tile
+                              frames, stored charge or timing */
     int32_t reserved0;
 } gc_params;
 
@@ -120,7 +123,8 @@ typedef struct {
     int64_t timed_steps;          /* with timing on: steps whose kernels were timed */
     int32_t device_loop;          /* 1: gc_run is one graph launch with a device-side loop
                                      (conditional WHILE node over passes of graph_steps steps) */
-    int32_t fused_path;           /* 1: the last gc_run ran steps on the fused small-workload path */
+    int32_t fused_path;           /* small-workload path of the last gc_run: 0 none, 1 two launches
+                                     per step, 2 the persistent single-event kernel */
 } gc_stats;
 
 /* Defaults: the CCD of the X-ray and muon workloads (thickness 675 um,
@@ -239,6 +243,17 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
 gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, double softening_um,
                                    double eps_si_rel, int32_t precision, double *E_dev,
                                    void *cuda_stream);
+
+/* Self-test of the library's bounded device-side wait (the grid barrier of
+ * the persistent single-event kernel; no counterpart in the paper): runs, on
+ * the current device, a barrier that waits for one block more than the grid
+ * has, so nothing can complete it.  Every block must give up after limit_s
+ * seconds (0 < limit_s <= 10) and report it.  Returns GC_ERR_DEVICE_TIMEOUT
+ * when the wait ran out as designed (the device stays usable), GC_OK if it
+ * did not, GC_ERR_NO_DEVICE without a GPU that supports cooperative launches.
+ * A simulation whose wait runs out returns GC_ERR_DEVICE_TIMEOUT from gc_run
+ * and must be destroyed. */
+gc_status gc_selftest_barrier_timeout(double limit_s);
 
 /* Free everything owned by the simulation (NULL is a no-op); the end of the
  * Sec. 3.2 run, after which no result of `s` can be read. */

@@ -17,6 +17,7 @@
 #include "gcoreccd.h"
 #include "gc_internal.cuh"
 #include "gc_launch.h"
+#include "gc_barrier.cuh"
 
 using namespace gc;
 
@@ -41,6 +42,10 @@ namespace {
         cudaError_t e_ = (call);                       \
         if (e_ != cudaSuccess) return cuda_fail(e_);   \
     } while (0)
+
+// Longest a device-side wait (a grid barrier of the persistent kernel) may
+// take before the kernel gives up with an error status.
+constexpr double kDeviceWaitLimitS = 1.0;
 
 // CODATA 2018 exact SI values and eps0.
 constexpr double kQ = 1.602176634e-19;
@@ -69,8 +74,9 @@ gc_status validate(const gc_params *p) {
     if (p->graph_steps < 0 || p->graph_steps > 4096) return GC_ERR_PARAM;
     if (p->jchunk < 0) return GC_ERR_PARAM;
     if ((p->coulomb | p->diffusion | p->reflect_back | p->autotune | p->newton | p->timing |
-         p->stored_charge | p->tile_frames | p->fuse_small) & ~1)
+         p->stored_charge | p->tile_frames) & ~1)
         return GC_ERR_PARAM;
+    if (p->fuse_small < 0 || p->fuse_small > 2) return GC_ERR_PARAM;
     if (p->pair_R != 0 && p->pair_R != 2 && p->pair_R != 4 && p->pair_R != 8) return GC_ERR_PARAM;
     return GC_OK;
 }
@@ -196,7 +202,9 @@ struct gc_sim {
     // holes are active (its own graph; the unfused graph hands over to it)
     bool fused_ok = false;
     int fused_grid = 0;
-    bool fused_ran = false;          // the last gc_run used the fused path
+    int fused_ran = 0;               // small-workload path of the last gc_run (gc_stats.fused_path)
+    bool se_ok = false;              // the persistent single-event kernel applies
+    int se_grid = 0;
     cudaGraphExec_t graph_small = nullptr;
     bool small_loops = false;
     int integ_grid = 1;
@@ -224,7 +232,8 @@ void free_state(gc_sim *s) {
             *g = nullptr;
         }
     s->fused_ok = false;
-    s->fused_ran = false;
+    s->fused_ran = 0;
+    s->se_ok = false;
     for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
         for (cudaEvent_t e : *v) cudaEventDestroy(e);
         v->clear();
@@ -727,6 +736,21 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         GC_ALLOC(d.tile_ticket, (N / 8 + E + 1) * 4)
         GC_ALLOC(d.keep8, N)
     }
+    // the persistent single-event kernel: one event, FP64 or FP32 without FP16x2
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+    s->se_ok = s->fused_ok && s->p.fuse_small == 1 && E == 1 && s->p.precision != GC_FP16X2 && coop;
+    if (s->se_ok) {
+        const size_t M = std::min<size_t>(N, kFusedMax);  // stable indices are slots at the launch
+        for (int b = 0; b < 2; ++b) {
+            if (fp64_mode(s)) {
+                GC_ALLOC(d.se_sh64[b], M * sizeof(double4_32a))
+            } else {
+                GC_ALLOC(d.se_sh32[b], M * sizeof(float4))
+            }
+            GC_ALLOC(d.se_keep[b], M)
+        }
+    }
     GC_ALLOC(d.ctrl, sizeof(Ctrl))
 #undef GC_ALLOC
     d.part_stride = (long long)N;
@@ -792,14 +816,19 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     }
     if (s->fused_ok) {
         s->fused_grid = s->sm_count * std::max(1, fused_pair_occupancy(s->p.precision, s->dev.shape.R));
-        if (!fused_pair_kernel_ptr(s->p.precision, s->dev.shape.R)) s->fused_ok = false;
+        if (!fused_pair_kernel_ptr(s->p.precision, s->dev.shape.R)) s->fused_ok = s->se_ok = false;
+    }
+    if (s->se_ok) {
+        const int occ = se_occupancy(s->p.precision, s->dev.shape.R);
+        s->se_grid = s->sm_count * occ;
+        if (occ < 1 || !se_kernel_ptr(s->p.precision, s->dev.shape.R)) s->se_ok = false;
     }
     r = set_limit(s, 0);
     if (r != GC_OK) return r;
     r = read_ctrl(s);
     if (r != GC_OK) return r;
     s->launches_per_step = (s->fused_ok && s->h_ctrl->n_active <= kFusedMax)
-                               ? 2
+                               ? (s->se_ok ? 0 : 2)
                                : (s->phys.coulomb ? 1 : 0) + (s->phys.stored ? 1 : 0) + (frames ? 1 : 0) + 3;
     if (s->p.timing) {
         for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
@@ -833,7 +862,20 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
         // are active, then (when available) the fused two-launch step.
         for (int phase = 0; phase < 2; ++phase) {
             const bool fz = s->fused_ok && s->h_ctrl->n_active <= kFusedMax;
-            if (fz) s->fused_ran = true;
+            if (fz && s->se_ok) {
+                // one event, few holes: the whole remaining loop in one cooperative launch
+                s->fused_ran = 2;
+                GC_CUDA(launch_se_loop(s->dev, s->p.precision, s->se_grid, kDeviceWaitLimitS, s->stream));
+                r = read_ctrl(s);
+                if (r != GC_OK) return r;
+                if (s->h_ctrl->error) {
+                    s->loaded = false;  // the state is undefined after a wait ran out
+                    return GC_ERR_DEVICE_TIMEOUT;
+                }
+                GC_CUDA(launch_build_items(s->dev, s->stream));  // items in the other paths' layout
+                break;
+            }
+            if (fz) s->fused_ran = 1;
             cudaGraphExec_t g = fz ? s->graph_small : s->graph;
             const bool loops = fz ? s->small_loops : s->graph_loops;
             if (use_graph(s) && !g) return GC_ERR_STATE;
@@ -993,7 +1035,7 @@ gc_status gc_get_stats(gc_sim *s, gc_stats *out) {
     out->compact_kernel_ms = s->compact_ms;
     out->timed_steps = s->timed_steps;
     out->device_loop = use_graph(s) && (!s->graph || s->graph_loops) && (!s->graph_small || s->small_loops);
-    out->fused_path = s->fused_ran ? 1 : 0;
+    out->fused_path = s->fused_ran;
     return GC_OK;
 }
 
@@ -1145,6 +1187,24 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
     cudaStreamSynchronize(st);
     m.release();
     return status;
+}
+
+gc_status gc_selftest_barrier_timeout(double limit_s) {
+    if (!(limit_s > 0) || !(limit_s <= 10.0)) return GC_ERR_PARAM;
+    int cnt = 0;
+    cudaError_t e = cudaGetDeviceCount(&cnt);
+    if (e != cudaSuccess || cnt == 0) {
+        if (e != cudaSuccess) cuda_fail(e);
+        return GC_ERR_NO_DEVICE;
+    }
+    int dev = 0, sms = 0, coop = 0;
+    GC_CUDA(cudaGetDevice(&dev));
+    GC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GC_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return GC_ERR_NO_DEVICE;
+    int bits = 0;
+    GC_CUDA(selftest_barrier_timeout(sms, limit_s, &bits, nullptr));
+    return (bits & kErrBarrierTimeout) ? GC_ERR_DEVICE_TIMEOUT : GC_OK;
 }
 
 void gc_destroy(gc_sim *s) {

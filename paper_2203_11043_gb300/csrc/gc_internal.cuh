@@ -52,6 +52,8 @@ struct Ctrl {
     unsigned long long pair_interactions; // sum over steps of sum_e n_e^2
     int error;               // device-detected inconsistency (bit flags)
     int tiles_total;         // i-tiles of the next step (fused small-workload path)
+    unsigned bar_count;      // grid barrier of the persistent single-event kernel:
+    unsigned bar_gen;        //   arrivals and generation
 };
 
 // Physics and geometry, precomputed on the host from gc_params.
@@ -117,6 +119,12 @@ struct Dev {
     int *tile_base;
     unsigned *tile_ticket;
     unsigned char *keep8;
+    // persistent single-event kernel: shadows indexed by a hole's stable index
+    // (its slot at the launch), two buffers read and written on alternate
+    // steps, and keep bytes per step parity
+    float4 *se_sh32[2];
+    double4_32a *se_sh64[2];
+    unsigned char *se_keep[2];
     Ctrl *ctrl;
     int n_total;
     int n_events;

@@ -55,6 +55,17 @@ const void *fused_pair_kernel_ptr(int precision, int R);
 int fused_pair_occupancy(int precision, int R);
 cudaError_t launch_fused_pair(const Dev &d, int precision, int grid, cudaStream_t st);
 cudaError_t launch_small_tail(const Dev &d, bool fp64, cudaStream_t st);
+// Persistent single-event kernel (one event of at most kFusedMax active holes,
+// FP64 form or FP32 forms without FP16x2, Newton step, tile frames or stored
+// charge): every step until completion or the step limit in one cooperative
+// launch of `grid` blocks (at most se_occupancy(...) per SM), one grid barrier
+// per step whose waits give up after limit_s (kErrBarrierTimeout).
+const void *se_kernel_ptr(int precision, int R);
+int se_occupancy(int precision, int R);
+cudaError_t launch_se_loop(const Dev &d, int precision, int grid, double limit_s, cudaStream_t st);
+// Runs a barrier that can never complete on `grid` co-resident blocks; the
+// error bits it leaves (kErrBarrierTimeout expected) go to *error_bits.
+cudaError_t selftest_barrier_timeout(int grid, double limit_s, int *error_bits, cudaStream_t st);
 // Recompute the pair work items from the current active offsets (after the
 // pair-kernel shape changes).
 cudaError_t launch_build_items(const Dev &d, cudaStream_t st);

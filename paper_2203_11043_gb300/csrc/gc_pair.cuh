@@ -54,11 +54,16 @@ namespace gc {
 // holes are taken between small FP32 numbers.  The j-tile origins reach
 // shared memory (s_fr) by cp.async with the tile before.  s_fr is written by
 // other threads, so it is not a restrict pointer.
-template <int R, bool KAHAN, bool NEWTON, int L, bool H16, bool TF>
+// LIST (the persistent single-event kernel): the event's shadow `shb` is
+// indexed by a hole's stable index, list[slot] in shared memory; otherwise
+// shb = sh32 + e_start is indexed by slot.
+template <int R, bool KAHAN, bool NEWTON, int L, bool H16, bool TF, bool LIST = false>
 __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int n_e, int local,
                                                  float scale, float *__restrict__ sx,
                                                  float *__restrict__ sy, float *__restrict__ sz,
-                                                 float4 *s_fr, float4 *s_raw) {
+                                                 float4 *s_fr, float4 *s_raw,
+                                                 const float4 *__restrict__ shb,
+                                                 const unsigned short *list = nullptr) {
     constexpr int G = 32 / L;
     constexpr int STRIDE = kPairThreads / L;
     constexpr int IB = R * STRIDE;
@@ -94,7 +99,7 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
         float4 a = make_float4(kSentinel, kSentinel, kSentinel, 0.f);
         const int ia = il0 + r * STRIDE;
         if (ia < n_e) {
-            a = d.sh32[e_start + ia];
+            a = LIST ? __ldcg(shb + list[ia]) : shb[ia];  // LIST: written by other SMs in this launch
             if (TF) {  // into the item frame
                 const int t = e_start + (ia & ~(kTileJ - 1));
                 const float4 th = d.frame_hi[t], tl = d.frame_lo[t];
@@ -131,7 +136,8 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int j = jt + u * kPairThreads + tid;
-            cp_async16_zfill(s_raw + u * kPairThreads + tid, d.sh32 + e_start + (j < j1 ? j : j0),
+            const int jj = j < j1 ? j : j0;
+            cp_async16_zfill(s_raw + u * kPairThreads + tid, shb + (LIST ? (int)list[jj] : jj),
                              j < j1 ? 16u : 0u);
         }
         if (TF && tid < 2)  // jt is a tile start (j-chunks are whole tiles)
@@ -342,10 +348,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
         const float scale = H16 ? h2_scale(__uint_as_float(ext[e])) : 1.0f;
         if (lanes_for(d.shape, n_e) == 1)
             pair_item_fp32_j<R, KAHAN, NEWTON, 1, H16, TF>(d, e_start, n_e, local, scale, s_x, s_y,
-                                                           s_z, s_fr, s_raw);
+                                                           s_z, s_fr, s_raw, d.sh32 + e_start);
         else
             pair_item_fp32_j<R, KAHAN, NEWTON, 4, H16, false>(d, e_start, n_e, local, scale, s_x, s_y,
-                                                              s_z, s_fr, s_raw);
+                                                              s_z, s_fr, s_raw, d.sh32 + e_start);
         if constexpr (FUSED) fused_tile_done<false>(d, e, e_start, n_e, local, cur, c->step + 1, &s_flag);
         __syncthreads();  // s_item and the tiles are reused by the next item
     }
@@ -358,10 +364,19 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
 // fraction of the FP32 rate on this GPU, so a few i-tiles would keep most SMs
 // idle): L = 16 lanes per carrier split each j-tile and combine with a fixed
 // xor-shuffle tree, 8 carriers per item, so the work spreads over the GPU.
-template <int L>
+// An FP64 shadow entry read through L2 (two 16-byte loads).
+__device__ __forceinline__ double4_32a ldcg_shadow64(const double4_32a *p) {
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return make_double4_32a(a.x, a.y, b.x, b.y);
+}
+
+template <int L, bool LIST = false>
 __device__ __forceinline__ void pair_item_fp64(const Dev &d, int e_start, int n_e, int local,
                                                double *__restrict__ s_x, double *__restrict__ s_y,
-                                               double *__restrict__ s_z) {
+                                               double *__restrict__ s_z,
+                                               const double4_32a *__restrict__ shb,
+                                               const unsigned short *list = nullptr) {
     constexpr int J = kPairThreads;      // j positions per shared tile
     constexpr int G = kPairThreads / L;  // carriers per item
     const int tid = threadIdx.x;
@@ -371,7 +386,7 @@ __device__ __forceinline__ void pair_item_fp64(const Dev &d, int e_start, int n_
     const int it = local / js, jc = local - it * js;
     const int il = it * G + g;
     double4_32a me = make_double4_32a(0, 0, 0, 0);
-    if (il < n_e) me = d.sh64[e_start + il];
+    if (il < n_e) me = LIST ? ldcg_shadow64(shb + list[il]) : shb[il];
     const double eps2 = d.phys.eps2;
     double ex = 0.0, ey = 0.0, ez = 0.0;
     const int j0 = jc * jchunk, j1 = min(n_e, j0 + jchunk);
@@ -379,7 +394,7 @@ __device__ __forceinline__ void pair_item_fp64(const Dev &d, int e_start, int n_
         __syncthreads();
         const int j = jt + tid;
         if (j < j1) {
-            const double4_32a q = d.sh64[e_start + j];
+            const double4_32a q = LIST ? ldcg_shadow64(shb + list[j]) : shb[j];
             s_x[tid] = q.x; s_y[tid] = q.y; s_z[tid] = q.z;
         }
         __syncthreads();
@@ -426,9 +441,9 @@ __global__ void __launch_bounds__(kPairThreads) pair_fp64_kernel(Dev d) {
         const int e_start = off[e], n_e = off[e + 1] - e_start;
         const int local = item - d.item_base[e];
         if (lanes_for(d.shape, n_e) == 1)
-            pair_item_fp64<1>(d, e_start, n_e, local, s_x, s_y, s_z);
+            pair_item_fp64<1>(d, e_start, n_e, local, s_x, s_y, s_z, d.sh64 + e_start);
         else
-            pair_item_fp64<16>(d, e_start, n_e, local, s_x, s_y, s_z);
+            pair_item_fp64<16>(d, e_start, n_e, local, s_x, s_y, s_z, d.sh64 + e_start);
         if constexpr (FUSED) fused_tile_done<true>(d, e, e_start, n_e, local, cur, c->step + 1, &s_flag);
         __syncthreads();
     }

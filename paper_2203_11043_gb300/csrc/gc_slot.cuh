@@ -122,15 +122,25 @@ __device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, 
 
 // ---- per-slot step -------------------------------------------------------------------
 // Returns true when the carrier stays active.
-// CG: read the per-chunk partial sums through L2 (ld.global.cg).  The fused
-// pair kernel integrates an i-tile in the same launch that wrote its partial
-// sums from other SMs, so this SM's L1 may hold a stale copy of their lines.
+// CG: read the per-chunk partial sums and the positions through L2
+// (ld.global.cg).  The fused kernels integrate an i-tile in the same launch
+// that wrote its partial sums (and, in the persistent kernel, its positions)
+// from other SMs, so this SM's L1 may hold a stale copy of their lines.
+// advance_hole: hole `id` of event e (n_e active holes; read only with the
+// Coulomb field on) whose per-chunk partial sums sit at slot p.
 template <bool F64, bool INIT, bool CG = false>
-__device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long long step) {
+__device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_e, int p, long long step) {
     const Phys &ph = d.phys;
-    const int id = d.act[cur][p];
-    const int e = d.ev_of_id[id];
-    double x = d.px[id], y = d.py[id], z = d.pz[id];
+    double x, y, z;
+    if (CG) {  // the persistent kernel integrates a hole on different SMs from step to step
+        x = __ldcg(d.px + id);
+        y = __ldcg(d.py + id);
+        z = __ldcg(d.pz + id);
+    } else {
+        x = d.px[id];
+        y = d.py[id];
+        z = d.pz[id];
+    }
     if (INIT) {
         if (ph.reflect && z > ph.thickness) {
             z = 2.0 * ph.thickness - z;
@@ -139,8 +149,6 @@ __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long 
     } else {
         double ex = 0.0, ey = 0.0, ez = 0.0;
         if (ph.coulomb) {  // Eq. 6: sum of the per-chunk partial sums, fixed order
-            const int *off = d.ev_off[cur];
-            const int n_e = off[e + 1] - off[e];
             const int js = ceil_div(n_e, d.shape.jchunk);
             const double *P = d.partial + p;
             for (int jc = 0; jc < js; ++jc) {
@@ -235,6 +243,19 @@ __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long 
         return false;
     }
     return true;
+}
+
+// advance_hole for the hole in slot p of the active list `cur`.
+template <bool F64, bool INIT, bool CG = false>
+__device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long long step) {
+    const int id = d.act[cur][p];
+    const int e = d.ev_of_id[id];
+    int n_e = 0;
+    if (!INIT && d.phys.coulomb) {
+        const int *off = d.ev_off[cur];
+        n_e = off[e + 1] - off[e];
+    }
+    return advance_hole<F64, INIT, CG>(d, id, e, n_e, p, step);
 }
 
 }  // namespace gc

@@ -26,7 +26,7 @@ GC_FP64, GC_FP32, GC_FP32_KAHAN, GC_FP16X2 = 0, 1, 2, 3
 EXPORTS = ("gc_default_params", "gc_create", "gc_load_carriers", "gc_run", "gc_collect",
            "gc_image", "gc_positions", "gc_get_stats", "gc_coulomb_field",
            "gc_coulomb_field_noalloc", "gc_save_state", "gc_restore_state", "gc_destroy",
-           "gc_status_string", "gc_last_cuda_error", "gc_device_info")
+           "gc_status_string", "gc_last_cuda_error", "gc_device_info", "gc_selftest_barrier_timeout")
 
 
 class GcParams(ctypes.Structure):
@@ -155,6 +155,8 @@ def load():
         L.gc_last_cuda_error.argtypes = []
         L.gc_device_info.restype = I32
         L.gc_device_info.argtypes = [ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]
+        L.gc_selftest_barrier_timeout.restype = I32
+        L.gc_selftest_barrier_timeout.argtypes = [ctypes.c_double]
         _lib = L
         return L
 
@@ -193,6 +195,12 @@ def gc_default_params(**overrides) -> GcParams:
             raise AttributeError(f"gc_params has no field {k}")
         setattr(p, k, v)
     return p
+
+
+def gc_selftest_barrier_timeout(limit_s: float) -> int:
+    """Status of the bounded-wait self-test (GC_ERR_DEVICE_TIMEOUT expected);
+    returned, not raised."""
+    return int(load().gc_selftest_barrier_timeout(float(limit_s)))
 
 
 def gc_device_info():

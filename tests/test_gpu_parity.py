@@ -510,30 +510,70 @@ def assert_same_run(a, b):
     assert a["stats"]["carrier_steps"] == b["stats"]["carrier_steps"]
 
 
-@pytest.mark.parametrize("precision", [0, 2, 3])
-def test_fused_small_step_equals_four_launch_step(gc, precision):
-    """While at most 8192 holes are active a step is two launches (pair kernel
-    that integrates each i-tile when its last j-chunk is summed, then one
-    compaction block).  It runs the same items, partial sums and per-carrier
-    arithmetic as the four-launch step, so the results are the same bits:
-    the 5.9 keV cloud and the ragged batch, with graphs and eagerly."""
-    for wl, kw in ((I.xray_5p9kev(), {}), (ragged_batch(), dict(pixel_um=1.0))):
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_small_paths_equal_four_launch_step(gc, precision):
+    """While at most 8192 holes are active a step can run as two launches (pair
+    kernel that integrates each i-tile when its last j-chunk is summed, then
+    one compaction block) or, for one event, inside the persistent kernel
+    that runs every remaining step in one cooperative launch.  Both run the
+    same items, partial sums and per-carrier arithmetic as the four-launch
+    step, so the results are the same bits: the 5.9 keV cloud and the ragged
+    batch, with graphs and eagerly."""
+    for wl, kw, single in ((I.xray_5p9kev(), {}, True), (ragged_batch(), dict(pixel_um=1.0), False)):
+        se = 2 if (single and precision != 3) else 1
         outs = []
-        for fuse, gs in ((0, 32), (1, 32), (1, 0)):
+        for fuse, gs, path in ((0, 32, 0), (2, 32, 1), (2, 0, 1), (1, 32, se), (1, 0, se)):
             res = run_gpu(gc, wl, precision, fuse_small=fuse, graph_steps=gs, **kw)
-            assert res["stats"]["fused_path"] == fuse
+            assert res["stats"]["fused_path"] == path, (fuse, gs)
             outs.append(res)
         for o in outs[1:]:
             assert_same_run(o, outs[0])
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_persistent_kernel_split_runs(gc, precision):
+    """The persistent kernel stops at the step limit of each gc_run and writes
+    the state back; runs split into pieces give the bits of one run."""
+    wl = I.single_cloud(n=700, sigma_um=0.4, z0_um=30.0, seed=19, img=32)
+    outs = []
+    for pieces in ([-1], [1, 7, 50, -1]):
+        p = gc.gc_default_params(precision=precision, img_w=32, img_h=32)
+        with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+            done = 0
+            for k in pieces:
+                done += sim.run(k)[1]
+            st = sim.stats()
+            assert st["fused_path"] == 2 and st["n_active"] == 0
+            outs.append((done, sim.positions(), sim.collect()["collect_step"], sim.image(),
+                         st["pair_interactions"], st["carrier_steps"]))
+    assert outs[0][0] == outs[1][0]
+    for a, b in zip(outs[0][1:], outs[1][1:]):
+        assert np.array_equal(a, b)
+    ref = run_oracle(wl)
+    assert np.array_equal(outs[0][2], ref.collect_step) or precision != 0
+
+
+def test_bounded_device_wait_reports_timeout(gc):
+    """The grid barrier of the persistent kernel gives up after its time limit
+    and reports it (a barrier that waits for a block that does not exist);
+    the device is usable afterwards."""
+    import time
+    t0 = time.time()
+    assert gc.gc_selftest_barrier_timeout(0.05) == gc.GC_ERR_DEVICE_TIMEOUT
+    assert time.time() - t0 < 10
+    wl = I.single_cloud(n=96, sigma_um=0.5, z0_um=20.0, seed=3, img=16)
+    res = run_gpu(gc, wl, 0)
+    assert_fp64_parity(res, run_oracle(wl), wl)
+
+
 def test_fused_takes_over_below_its_limit(gc):
-    """A 12,000-hole cloud starts on the four-launch step and hands over to the
-    fused one once at most 8192 holes are active; the whole run is the same
-    bits as a run on the four-launch step throughout."""
+    """A 12,000-hole cloud starts on the four-launch step and hands over to a
+    small-workload path once at most 8192 holes are active; the whole run is
+    the same bits as a run on the four-launch step throughout."""
     wl = I.single_cloud(n=12000, sigma_um=0.6, z0_um=20.0, seed=44, img=32)
     a = run_gpu(gc, wl, 2, fuse_small=0)
-    b = run_gpu(gc, wl, 2, fuse_small=1)
-    assert a["stats"]["fused_path"] == 0 and b["stats"]["fused_path"] == 1
-    assert_same_run(a, b)
-    assert b["status"] == 0 and b["stats"]["n_active"] == 0
+    for fuse, path in ((2, 1), (1, 2)):
+        b = run_gpu(gc, wl, 2, fuse_small=fuse)
+        assert a["stats"]["fused_path"] == 0 and b["stats"]["fused_path"] == path
+        assert_same_run(a, b)
+        assert b["status"] == 0 and b["stats"]["n_active"] == 0
