@@ -736,12 +736,13 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         GC_ALLOC(d.tile_ticket, (N / 8 + E + 1) * 4)
         GC_ALLOC(d.keep8, N)
     }
-    // the persistent single-event kernel: one event, FP64 or FP32 without FP16x2
+    // the persistent single-event kernel: one event, FP64 or FP32 without FP16x2;
+    // its shadows and keep bytes (keep bytes by slot, shadows by hole id)
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
     s->se_ok = s->fused_ok && s->p.fuse_small == 1 && E == 1 && s->p.precision != GC_FP16X2 && coop;
     if (s->se_ok) {
-        const size_t M = std::min<size_t>(N, kFusedMax);  // stable indices are slots at the launch
+        const size_t M = N;  // indexed by hole id
         for (int b = 0; b < 2; ++b) {
             if (fp64_mode(s)) {
                 GC_ALLOC(d.se_sh64[b], M * sizeof(double4_32a))
@@ -865,7 +866,13 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
             if (fz && s->se_ok) {
                 // one event, few holes: the whole remaining loop in one cooperative launch
                 s->fused_ran = 2;
-                GC_CUDA(launch_se_loop(s->dev, s->p.precision, s->se_grid, kDeviceWaitLimitS, s->stream));
+                // at most one block per work item of the first step (fewer arrivals per barrier)
+                const int na = s->h_ctrl->n_active;
+                const PairShape &sh = s->dev.shape;
+                const long long items = (long long)ceil_div(na, itile_for(sh.R, lanes_for(sh, na))) *
+                                        ceil_div(na, sh.jchunk);
+                const int grid = (int)std::max(1LL, std::min<long long>(s->se_grid, items));
+                GC_CUDA(launch_se_loop(s->dev, s->p.precision, grid, kDeviceWaitLimitS, s->stream));
                 r = read_ctrl(s);
                 if (r != GC_OK) return r;
                 if (s->h_ctrl->error) {

@@ -55,15 +55,15 @@ namespace gc {
 // shared memory (s_fr) by cp.async with the tile before.  s_fr is written by
 // other threads, so it is not a restrict pointer.
 // LIST (the persistent single-event kernel): the event's shadow `shb` is
-// indexed by a hole's stable index, list[slot] in shared memory; otherwise
-// shb = sh32 + e_start is indexed by slot.
+// indexed by hole id, list[slot] in shared memory; otherwise shb = sh32 +
+// e_start is indexed by slot.
 template <int R, bool KAHAN, bool NEWTON, int L, bool H16, bool TF, bool LIST = false>
 __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int n_e, int local,
                                                  float scale, float *__restrict__ sx,
                                                  float *__restrict__ sy, float *__restrict__ sz,
                                                  float4 *s_fr, float4 *s_raw,
                                                  const float4 *__restrict__ shb,
-                                                 const unsigned short *list = nullptr) {
+                                                 const int *list = nullptr) {
     constexpr int G = 32 / L;
     constexpr int STRIDE = kPairThreads / L;
     constexpr int IB = R * STRIDE;
@@ -376,7 +376,7 @@ __device__ __forceinline__ void pair_item_fp64(const Dev &d, int e_start, int n_
                                                double *__restrict__ s_x, double *__restrict__ s_y,
                                                double *__restrict__ s_z,
                                                const double4_32a *__restrict__ shb,
-                                               const unsigned short *list = nullptr) {
+                                               const int *list = nullptr) {
     constexpr int J = kPairThreads;      // j positions per shared tile
     constexpr int G = kPairThreads / L;  // carriers per item
     const int tid = threadIdx.x;

@@ -5,13 +5,16 @@
 // dependent memory round trips per kernel; a launch per stage (or two, in
 // the fused path) pays that chain again and again.  Here every block stays
 // resident for all steps:
+//   0. (once per launch) the shadow is copied into a buffer indexed by hole
+//      id, then one grid barrier;
 //   1. pair + integrate: blocks take the step's pair work items (the same
 //      items, partial sums and per-carrier arithmetic as the other paths);
 //      the item that completes an i-tile's j-chunks integrates that i-tile
-//      and writes each kept hole's next shadow at the hole's stable index;
+//      and writes each kept hole's next shadow at the hole's id;
 //   2. one grid barrier (bounded in time, gc_barrier.cuh);
-//   3. every block compacts its own copy of the slot list (shared memory)
-//      from the step's keep bytes, so no data moves between steps.
+//   3. every block compacts its own copy of the active list (hole ids, in
+//      shared memory) from the step's keep bytes, so no data moves between
+//      steps.
 // Slot numbering, j order and partial sums are those of the compacted active
 // list of the four-launch step, so the results are the same bits.  At the end
 // block 0 writes the state back in the layout of the other paths.
@@ -23,14 +26,13 @@
 
 namespace gc {
 
-constexpr int kSEListBytes = kFusedMax * 2;  // dynamic shared memory: the slot list (uint16)
+constexpr int kSEListBytes = kFusedMax * 4;  // dynamic shared memory: the active list (hole ids)
 
 // After one pair item (slots of event 0 numbered by the current list): the
 // item that completes its i-tile integrates the tile's holes.
 template <bool F64, typename Shadow>
 __device__ __forceinline__ void se_tile_done(const Dev &d, int n, int local, int js, int itile, long long step,
-                                             const int *__restrict__ act0, const unsigned short *list,
-                                             unsigned char *keep, Shadow *wr, int *s_flag) {
+                                             const int *list, unsigned char *keep, Shadow *wr, int *s_flag) {
     const int it = local / js;
     __threadfence();
     __syncthreads();
@@ -47,36 +49,34 @@ __device__ __forceinline__ void se_tile_done(const Dev &d, int n, int local, int
     const double ox = d.ev_origin[0], oy = d.ev_origin[1], oz = d.ev_origin[2];
     const int i1 = min(n, (it + 1) * itile);
     for (int q = it * itile + (int)threadIdx.x; q < i1; q += blockDim.x) {
-        const int orig = list[q];
-        const int id = act0[orig];
+        const int id = list[q];
         const bool kept = advance_hole<F64, false, true>(d, id, 0, n, q, step);
         keep[q] = kept ? 1 : 0;
         if (kept) {  // the shadow of the next step, as the compaction writes it
             if constexpr (F64)
-                wr[orig] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
+                wr[id] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
             else
-                wr[orig] = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy), (float)(d.pz[id] - oz),
-                                       1.0f);
+                wr[id] = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy), (float)(d.pz[id] - oz),
+                                     1.0f);
         }
     }
 }
 
 // Stable in-place compaction of list[0..n) by keep (written by other blocks:
-// read through L2), in rounds of 8 slots per thread; returns the new length.
-__device__ __forceinline__ int se_compact_list(unsigned short *list, const unsigned char *keep, int n,
-                                               long long *s_warp) {
-    constexpr int PER = 8;
+// read through L2), in rounds of 16 slots per thread; returns the new length.
+__device__ __forceinline__ int se_compact_list(int *list, const unsigned char *keep, int n, long long *s_warp) {
+    constexpr int PER = 16;
     int base = 0;
     for (int c0 = 0; c0 < n; c0 += PER * (int)blockDim.x) {
         const int p0 = c0 + (int)threadIdx.x * PER;
-        unsigned short v[PER];
+        int v[PER];
         unsigned char kb[PER];
         int cnt = 0;
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int p = p0 + u;
             kb[u] = p < n ? __ldcg(keep + p) : (unsigned char)0;
-            v[u] = p < n ? list[p] : (unsigned short)0;
+            v[u] = p < n ? list[p] : 0;
             cnt += kb[u];
         }
         long long tot;
@@ -90,9 +90,10 @@ __device__ __forceinline__ int se_compact_list(unsigned short *list, const unsig
     return base;
 }
 
+// FP64: the pair term is FP64-latency bound, so keep 5 blocks (20 warps) per SM.
 template <int R, bool KAHAN, bool F64>
-__global__ void __launch_bounds__(kPairThreads, 1) se_loop_kernel(Dev d, unsigned long long limit_ns) {
-    extern __shared__ unsigned short s_list[];  // kFusedMax slots
+__global__ void __launch_bounds__(kPairThreads, F64 ? 5 : 1) se_loop_kernel(Dev d, unsigned long long limit_ns) {
+    extern __shared__ int s_list[];  // the active list: kFusedMax hole ids
     __shared__ __align__(16) float s_x[4 * kTileJ], s_y[4 * kTileJ], s_z[4 * kTileJ];
     __shared__ __align__(16) float4 s_raw[4 * kTileJ];
     __shared__ float4 s_fr[1];
@@ -106,8 +107,13 @@ __global__ void __launch_bounds__(kPairThreads, 1) se_loop_kernel(Dev d, unsigne
     const int cur = c->cur;
     const int *act0 = d.act[cur];
     int n = c->n_active;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) s_list[q] = (unsigned short)q;
-    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += blockDim.x) s_list[q] = act0[q];
+    // the shadow of the first step, indexed by hole id
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        if constexpr (F64) d.se_sh64[0][act0[q]] = d.sh64[q];
+        else d.se_sh32[0][act0[q]] = d.sh32[q];
+    }
+    if (!grid_barrier(&c->bar_count, &c->bar_gen, &c->error, gridDim.x, limit_ns, &s_ok)) return;
     unsigned long long pairs = 0, csteps = 0;
     int k = 0;
     for (;; ++k) {
@@ -115,10 +121,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) se_loop_kernel(Dev d, unsigne
         const Shadow *rd;
         Shadow *wr;
         if constexpr (F64) {
-            rd = k == 0 ? d.sh64 : d.se_sh64[k & 1];
+            rd = d.se_sh64[k & 1];
             wr = d.se_sh64[(k + 1) & 1];
         } else {
-            rd = k == 0 ? d.sh32 : d.se_sh32[k & 1];
+            rd = d.se_sh32[k & 1];
             wr = d.se_sh32[(k + 1) & 1];
         }
         const int L = lanes_for(d.shape, n);
@@ -139,7 +145,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) se_loop_kernel(Dev d, unsigne
                     pair_item_fp32_j<R, KAHAN, false, 4, false, false, true>(d, 0, n, item, 1.0f, s_x, s_y, s_z,
                                                                            s_fr, s_raw, rd, s_list);
             }
-            se_tile_done<F64>(d, n, item, js, itile, step + 1, act0, s_list, keep, wr, &s_flag);
+            se_tile_done<F64>(d, n, item, js, itile, step + 1, s_list, keep, wr, &s_flag);
             __syncthreads();  // shared tiles and s_flag are reused by the next item
         }
         if (!grid_barrier(&c->bar_count, &c->bar_gen, &c->error, gridDim.x, limit_ns, &s_ok)) return;
@@ -158,10 +164,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) se_loop_kernel(Dev d, unsigne
     if constexpr (F64) last = d.se_sh64[(k + 1) & 1]; else last = d.se_sh32[(k + 1) & 1];
     int *dst = d.act[cur ^ 1];
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        const int orig = s_list[q];
-        dst[q] = act0[orig];
-        if constexpr (F64) sh[q] = ldcg_shadow64(last + orig);  // written by other SMs
-        else sh[q] = __ldcg(last + orig);
+        const int id = s_list[q];
+        dst[q] = id;
+        if constexpr (F64) sh[q] = ldcg_shadow64(last + id);  // written by other SMs
+        else sh[q] = __ldcg(last + id);
     }
     if (threadIdx.x == 0) {
         d.ev_off[cur ^ 1][0] = 0;
@@ -193,9 +199,15 @@ const void *se_kernel_ptr(int precision, int R) {
     return nullptr;
 }
 
+// The active list (dynamic) plus the static tiles exceed the default 48 KB
+// per block: opt in to the larger dynamic size.
+static cudaError_t se_prepare(const void *k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSEListBytes);
+}
+
 int se_occupancy(int precision, int R) {
     const void *k = se_kernel_ptr(precision, R);
-    if (!k) return 0;
+    if (!k || se_prepare(k) != cudaSuccess) return 0;
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kPairThreads, kSEListBytes) != cudaSuccess)
         return 0;
@@ -205,6 +217,8 @@ int se_occupancy(int precision, int R) {
 cudaError_t launch_se_loop(const Dev &d, int precision, int grid, double limit_s, cudaStream_t st) {
     const void *k = se_kernel_ptr(precision, d.shape.R);
     if (!k || grid < 1) return cudaErrorInvalidValue;
+    cudaError_t e = se_prepare(k);
+    if (e != cudaSuccess) return e;
     Dev dd = d;
     unsigned long long limit_ns = (unsigned long long)(limit_s * 1e9);
     void *args[] = {(void *)&dd, (void *)&limit_ns};
