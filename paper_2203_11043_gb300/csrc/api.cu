@@ -749,7 +749,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
             } else {
                 GC_ALLOC(d.se_sh32[b], M * sizeof(float4))
             }
-            GC_ALLOC(d.se_keep[b], M)
+            GC_ALLOC(d.se_keep[b], (M + 15) / 16 * 16)  // whole 16-byte words (vector loads)
         }
     }
     GC_ALLOC(d.ctrl, sizeof(Ctrl))

@@ -22,6 +22,12 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
 __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Release/acquire fence at GPU scope.  Issued by thread 0 after a block-wide
+// barrier it orders the whole block's earlier writes (the pattern of a
+// cooperative-groups grid sync); readers of data written by other SMs within
+// the same launch load through L2 (ld.global.cg).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -32,9 +38,9 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // every block must call it; returns false for the whole block on timeout.
 __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, int *error, unsigned expected,
                                              unsigned long long limit_ns, int *s_ok) {
-    __threadfence();  // this thread's writes before the arrival
-    __syncthreads();
+    __syncthreads();  // the block's writes before thread 0's release
     if (threadIdx.x == 0) {
+        fence_acq_rel_gpu();
         const unsigned g = ld_acquire_gpu(gen);
         int ok = 1;
         if (atomicAdd(count, 1u) == expected - 1) {
@@ -53,10 +59,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, int
         }
         *s_ok = ok;
     }
-    __syncthreads();
-    const bool ok = *s_ok != 0;
-    __threadfence();  // the other blocks' writes are visible from here on
-    return ok;
+    __syncthreads();  // thread 0's acquire covers the block from here on
+    return *s_ok != 0;
 }
 
 }  // namespace gc

@@ -54,6 +54,7 @@ struct Ctrl {
     int tiles_total;         // i-tiles of the next step (fused small-workload path)
     unsigned bar_count;      // grid barrier of the persistent single-event kernel:
     unsigned bar_gen;        //   arrivals and generation
+    unsigned se_item[2];     // its work-item counters, by step parity (FP64 form)
 };
 
 // Physics and geometry, precomputed on the host from gc_params.

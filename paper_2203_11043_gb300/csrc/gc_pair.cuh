@@ -273,8 +273,8 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
     }
 }
 
-// Fused small-workload path, after one pair item: every thread fences its
-// partial-sum stores, thread 0 counts the item on its i-tile's ticket, and the
+// Fused small-workload path, after one pair item: the block's partial-sum
+// stores are released by thread 0, which counts the item on its i-tile's ticket, and the
 // item that brings the ticket to the number of j-chunks integrates the
 // i-tile's carriers (reading the partials through L2) and writes their keep
 // bytes.  The ticket is reset for the next step by that item.  No block ever
@@ -285,18 +285,20 @@ __device__ __forceinline__ void fused_tile_done(const Dev &d, int e, int e_start
     const int itile = itile_for(d.shape.R, lanes_for(d.shape, n_e));
     const int js = ceil_div(n_e, d.shape.jchunk);
     const int it = local / js;
-    __threadfence();
-    __syncthreads();
+    __syncthreads();  // the block's partial sums before thread 0's release
     if (threadIdx.x == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         unsigned *t = d.tile_ticket + d.tile_base[e] + it;
         const unsigned done = atomicAdd(t, 1u);
         const int last = done == (unsigned)(js - 1);
-        if (last) *t = 0u;
+        if (last) {
+            *t = 0u;
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: the other items' partial sums
+        }
         *s_flag = last;
     }
     __syncthreads();
     if (*s_flag) {
-        __threadfence();
         const int i1 = min(n_e, (it + 1) * itile);
         for (int q = it * itile + (int)threadIdx.x; q < i1; q += blockDim.x) {
             const int p = e_start + q;

@@ -127,20 +127,12 @@ __device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, 
 // that wrote its partial sums (and, in the persistent kernel, its positions)
 // from other SMs, so this SM's L1 may hold a stale copy of their lines.
 // advance_hole: hole `id` of event e (n_e active holes; read only with the
-// Coulomb field on) whose per-chunk partial sums sit at slot p.
+// Coulomb field on) at (x, y, z), whose per-chunk partial sums sit at slot p;
+// on return (x, y, z) is the new position (also stored).
 template <bool F64, bool INIT, bool CG = false>
-__device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_e, int p, long long step) {
+__device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_e, int p, long long step,
+                                             double &x, double &y, double &z) {
     const Phys &ph = d.phys;
-    double x, y, z;
-    if (CG) {  // the persistent kernel integrates a hole on different SMs from step to step
-        x = __ldcg(d.px + id);
-        y = __ldcg(d.py + id);
-        z = __ldcg(d.pz + id);
-    } else {
-        x = d.px[id];
-        y = d.py[id];
-        z = d.pz[id];
-    }
     if (INIT) {
         if (ph.reflect && z > ph.thickness) {
             z = 2.0 * ph.thickness - z;
@@ -150,18 +142,36 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
         double ex = 0.0, ey = 0.0, ez = 0.0;
         if (ph.coulomb) {  // Eq. 6: sum of the per-chunk partial sums, fixed order
             const int js = ceil_div(n_e, d.shape.jchunk);
+            const long long st = d.part_stride;
             const double *P = d.partial + p;
-            for (int jc = 0; jc < js; ++jc) {
-                if (CG) {
-                    ex += __ldcg(P);
-                    ey += __ldcg(P + d.part_stride);
-                    ez += __ldcg(P + 2 * d.part_stride);
-                } else {
-                    ex += P[0];
-                    ey += P[d.part_stride];
-                    ez += P[2 * d.part_stride];
+            // loads of up to 8 chunks are issued before their (ordered) sums,
+            // so the chunk count does not chain memory round trips
+            constexpr int B = 8;
+            for (int jc0 = 0; jc0 < js; jc0 += B) {
+                double v[B][3];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    if (jc0 + u < js) {
+                        const double *Q = P + (long long)(jc0 + u) * 3 * st;
+                        if (CG) {
+                            v[u][0] = __ldcg(Q);
+                            v[u][1] = __ldcg(Q + st);
+                            v[u][2] = __ldcg(Q + 2 * st);
+                        } else {
+                            v[u][0] = Q[0];
+                            v[u][1] = Q[st];
+                            v[u][2] = Q[2 * st];
+                        }
+                    }
                 }
-                P += 3 * d.part_stride;
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    if (jc0 + u < js) {
+                        ex += v[u][0];
+                        ey += v[u][1];
+                        ez += v[u][2];
+                    }
+                }
             }
             ex *= ph.K;
             ey *= ph.K;
@@ -255,7 +265,17 @@ __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long 
         const int *off = d.ev_off[cur];
         n_e = off[e + 1] - off[e];
     }
-    return advance_hole<F64, INIT, CG>(d, id, e, n_e, p, step);
+    double x, y, z;
+    if (CG) {  // the fused kernels may integrate a hole on another SM than the last write
+        x = __ldcg(d.px + id);
+        y = __ldcg(d.py + id);
+        z = __ldcg(d.pz + id);
+    } else {
+        x = d.px[id];
+        y = d.py[id];
+        z = d.pz[id];
+    }
+    return advance_hole<F64, INIT, CG>(d, id, e, n_e, p, step, x, y, z);
 }
 
 }  // namespace gc

@@ -30,52 +30,68 @@ constexpr int kSEListBytes = kFusedMax * 4;  // dynamic shared memory: the activ
 
 // After one pair item (slots of event 0 numbered by the current list): the
 // item that completes its i-tile integrates the tile's holes.
+// (x, y, z): the position of this thread's hole of the i-tile (preloaded).
 template <bool F64, typename Shadow>
 __device__ __forceinline__ void se_tile_done(const Dev &d, int n, int local, int js, int itile, long long step,
-                                             const int *list, unsigned char *keep, Shadow *wr, int *s_flag) {
+                                             const int *list, unsigned char *keep, Shadow *wr, int *s_flag,
+                                             double x, double y, double z) {
     const int it = local / js;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    __syncthreads();  // the block's partial sums before thread 0's release (or own use)
+    if (js == 1) {
+        // one j-chunk: this item completes its i-tile
+    } else if (threadIdx.x == 0) {
+        fence_acq_rel_gpu();
         unsigned *t = d.tile_ticket + it;
         const unsigned done = atomicAdd(t, 1u);
         const int last = done == (unsigned)(js - 1);
-        if (last) *t = 0u;
+        if (last) {
+            *t = 0u;
+            fence_acq_rel_gpu();  // acquire: the other items' partial sums (read through L2)
+        }
         *s_flag = last;
     }
-    __syncthreads();
-    if (!*s_flag) return;
-    __threadfence();
+    if (js > 1) {
+        __syncthreads();
+        if (!*s_flag) return;
+    }
     const double ox = d.ev_origin[0], oy = d.ev_origin[1], oz = d.ev_origin[2];
     const int i1 = min(n, (it + 1) * itile);
-    for (int q = it * itile + (int)threadIdx.x; q < i1; q += blockDim.x) {
+    bool first = true;  // the first hole's position was preloaded; larger i-tiles load the rest here
+    for (int q = it * itile + (int)threadIdx.x; q < i1; q += blockDim.x, first = false) {
         const int id = list[q];
-        const bool kept = advance_hole<F64, false, true>(d, id, 0, n, q, step);
-        keep[q] = kept ? 1 : 0;
+        if (!first) {
+            x = __ldcg(d.px + id);
+            y = __ldcg(d.py + id);
+            z = __ldcg(d.pz + id);
+        }
+        const bool kept = advance_hole<F64, false, true>(d, id, 0, n, q, step, x, y, z);
         if (kept) {  // the shadow of the next step, as the compaction writes it
             if constexpr (F64)
-                wr[id] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
+                wr[id] = make_double4_32a(x - ox, y - oy, z - oz, 0.0);
             else
-                wr[id] = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy), (float)(d.pz[id] - oz),
-                                     1.0f);
+                wr[id] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 1.0f);
         }
+        keep[q] = kept ? 1 : 0;
     }
 }
 
 // Stable in-place compaction of list[0..n) by keep (written by other blocks:
 // read through L2), in rounds of 16 slots per thread; returns the new length.
 __device__ __forceinline__ int se_compact_list(int *list, const unsigned char *keep, int n, long long *s_warp) {
-    constexpr int PER = 16;
+    constexpr int PER = 16;  // one 16-byte load of keep bytes per thread and round
     int base = 0;
     for (int c0 = 0; c0 < n; c0 += PER * (int)blockDim.x) {
         const int p0 = c0 + (int)threadIdx.x * PER;
         int v[PER];
         unsigned char kb[PER];
         int cnt = 0;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (p0 < n) w = __ldcg(reinterpret_cast<const uint4 *>(keep + p0));  // keep is 16-byte aligned
+        const unsigned wv[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int p = p0 + u;
-            kb[u] = p < n ? __ldcg(keep + p) : (unsigned char)0;
+            kb[u] = p < n ? (unsigned char)((wv[u >> 2] >> (8 * (u & 3))) & 0xffu) : (unsigned char)0;
             v[u] = p < n ? list[p] : 0;
             cnt += kb[u];
         }
@@ -131,7 +147,28 @@ __global__ void __launch_bounds__(kPairThreads, F64 ? 5 : 1) se_loop_kernel(Dev 
         const int itile = itile_for(d.shape.R, L);
         const int js = ceil_div(n, d.shape.jchunk);
         const int items = ceil_div(n, itile) * js;
-        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        // FP32: one or a few items per block, assigned round-robin; FP64: many
+        // long items, taken from a counter (reset by block 0 after the step's barrier)
+        for (int item = F64 ? -1 : (int)blockIdx.x;; item += gridDim.x) {
+            if constexpr (F64) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_flag = (int)atomicAdd(&c->se_item[k & 1], 1u);
+                __syncthreads();
+                item = s_flag;
+            }
+            if (item >= items) break;
+            // this thread's hole of the item's i-tile: its position is loaded now, so that
+            // the integration after the pair sum waits on no memory but the partial sums
+            double hx = 0.0, hy = 0.0, hz = 0.0;
+            {
+                const int q = (item / js) * itile + (int)threadIdx.x;
+                if ((int)threadIdx.x < itile && q < n) {  // the first hole this thread integrates
+                    const int id = s_list[q];
+                    hx = __ldcg(d.px + id);
+                    hy = __ldcg(d.py + id);
+                    hz = __ldcg(d.pz + id);
+                }
+            }
             if constexpr (F64) {
                 double *tx = reinterpret_cast<double *>(s_x), *ty = reinterpret_cast<double *>(s_y),
                        *tz = reinterpret_cast<double *>(s_z);
@@ -145,10 +182,11 @@ __global__ void __launch_bounds__(kPairThreads, F64 ? 5 : 1) se_loop_kernel(Dev 
                     pair_item_fp32_j<R, KAHAN, false, 4, false, false, true>(d, 0, n, item, 1.0f, s_x, s_y, s_z,
                                                                            s_fr, s_raw, rd, s_list);
             }
-            se_tile_done<F64>(d, n, item, js, itile, step + 1, s_list, keep, wr, &s_flag);
+            se_tile_done<F64>(d, n, item, js, itile, step + 1, s_list, keep, wr, &s_flag, hx, hy, hz);
             __syncthreads();  // shared tiles and s_flag are reused by the next item
         }
         if (!grid_barrier(&c->bar_count, &c->bar_gen, &c->error, gridDim.x, limit_ns, &s_ok)) return;
+        if (F64 && blockIdx.x == 0 && threadIdx.x == 0) c->se_item[k & 1] = 0u;  // every block is past its items
         pairs += (unsigned long long)n * (unsigned long long)n;
         csteps += (unsigned long long)n;
         n = se_compact_list(s_list, keep, n, s_warp);
