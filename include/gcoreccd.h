@@ -76,7 +76,10 @@ typedef struct {
     int32_t img_w, img_h;  /* image size in pixels per event */
     double pixel_um;       /* pixel pitch (Fig. 5: 15 um) */
     int32_t graph_steps;   /* time steps per captured CUDA graph; 0 = eager launches */
-    int32_t autotune;      /* 1: time candidate pair-kernel shapes at load and keep the fastest */
+    int32_t autotune;      /* 1: pick the pair-kernel shape (carriers per thread, kernel variant,
+                              resident blocks per SM, j-chunk length, 4-lane threshold) by timing
+                              candidates on sampled work items of the loaded carriers; the choice
+                              is cached in the process per device, form and event-size histogram */
     int32_t newton;        /* 1: one Newton step after the MUFU rsqrt (FP32 forms) */
     int32_t jchunk;        /* j-chunk length of a pair work item; 0 = automatic */
     int32_t pair_R;        /* carriers per thread in the FP32 pair kernel (2, 4, 8); 0 = automatic */
@@ -125,6 +128,13 @@ typedef struct {
                                      (conditional WHILE node over passes of graph_steps steps) */
     int32_t fused_path;           /* small-workload path of the last gc_run: 0 none, 1 two launches
                                      per step, 2 the persistent single-event kernel */
+    double tune_ms;               /* autotuner: host time spent choosing the pair-kernel shape at the
+                                     last gc_load_carriers (0 when cached or off) */
+    int32_t tune_candidates;      /* shapes timed at the last load */
+    int32_t tune_cached;          /* 1: the shape came from the in-process autotuner cache */
+    int32_t pair_kernel_variant;  /* FP32 pair-kernel variant in use (0 default, 1 fewer loads in
+                                     flight, 2 one more resident block per SM) */
+    int32_t small_n;              /* events below this many active holes use 4 lanes per carrier */
 } gc_stats;
 
 /* Defaults: the CCD of the X-ray and muon workloads (thickness 675 um,

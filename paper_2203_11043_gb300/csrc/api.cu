@@ -7,11 +7,15 @@
 // Every step of the transport itself runs in the kernels of pair.cu and
 // step.cu.
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "gcoreccd.h"
@@ -205,6 +209,10 @@ struct gc_sim {
     int fused_ran = 0;               // small-workload path of the last gc_run (gc_stats.fused_path)
     bool se_ok = false;              // the persistent single-event kernel applies
     int se_grid = 0;
+    unsigned *h_probe = nullptr;     // pinned: items_total, work_counter of an autotuner probe
+    double tune_ms = 0.0;            // autotuner: host time spent at the last load
+    int tune_candidates = 0;         //   shapes timed
+    int tune_cached = 0;             //   1: the shape came from the in-process cache
     cudaGraphExec_t graph_small = nullptr;
     bool small_loops = false;
     int integ_grid = 1;
@@ -414,56 +422,255 @@ PairShape gc::field_shape(int precision, int sm_count, long long n, long long ma
 
 namespace {
 
-// Pick R (and the grid and j-chunk that follow from it) for the FP32 pair
-// kernel.  With autotune on, each candidate is timed on the loaded carriers.
+// ---- autotuner ----------------------------------------------------------------
+// Knobs of the FP32 pair kernel: R (carriers per thread), the kernel variant V
+// (loads in flight, register budget), resident blocks per SM, the j-chunk
+// target (work items per resident block) and the 4-lane threshold.  R, V and
+// the blocks per SM do not change any result; the j-chunk and the threshold
+// change the order of the FP32 partial sums (within the same error bound).
+struct TuneKnobs {
+    int R = 4, V = 0, bps = 0, small_n = kSmallEvent, target = 32;
+};
+
+struct TuneResult {
+    TuneKnobs k;
+    bool valid = false;
+};
+
+std::mutex g_tune_mutex;
+std::map<std::string, TuneKnobs> g_tune_cache;  // in-process: device, form and workload shape -> knobs
+
+// Cache key: device, form, user overrides and the workload's event-size
+// histogram in powers of two (event count, largest event, sum of n^2, events
+// below each lane threshold candidate).
+std::string tune_key(const gc_sim *s, const std::vector<long long> &sizes) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, s->device);
+    long long n_max = 1, ev = 0, small1 = 0, small2 = 0, small4 = 0;
+    double pairs = 0.0;
+    for (long long n : sizes) {
+        if (n <= 0) continue;
+        ++ev;
+        n_max = std::max(n_max, n);
+        pairs += (double)n * (double)n;
+        small1 += n < 1024;
+        small2 += n < 2048;
+        small4 += n < 4096;
+    }
+    auto lg = [](double v) { return v > 0 ? (int)std::floor(std::log2(v)) : -1; };
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|%d|p%d|n%d|t%d|R%d|j%d|E%d|N%d|P%d|s%d.%d.%d", prop.name,
+                  prop.multiProcessorCount, s->p.precision, s->p.newton, s->dev.tile_frames, s->p.pair_R,
+                  s->p.jchunk, lg((double)ev), lg((double)n_max), lg(pairs), lg((double)small1),
+                  lg((double)small2), lg((double)small4));
+    return buf;
+}
+
+// The pair shape of a set of knobs; n_blocks = 0 when the kernel is not built
+// or cannot hold that many blocks per SM.
+PairShape shape_of(const gc_sim *s, const std::vector<long long> &sizes, const TuneKnobs &k) {
+    PairShape sh{};
+    sh.R = k.R;
+    sh.V = k.V;
+    sh.small_n = k.small_n;
+    sh.small_lanes = 4;
+    const int occ = pair_kernel_occupancy(s->p.precision, k.R, s->p.newton, s->dev.tile_frames, k.V);
+    const int bps = k.bps > 0 ? k.bps : occ;
+    sh.n_blocks = (occ > 0 && bps <= occ) ? s->sm_count * bps : 0;
+    PairShape ref = sh;
+    ref.n_blocks = std::max(1, std::max(1, sh.n_blocks) * k.target / 32);  // items per block = target
+    sh.jchunk = choose_jchunk(sizes, ref, s->p.jchunk, kTileJ);
+    return sh;
+}
+
+// Work items of shape sh for the active event sizes (internal event order),
+// and the pair terms of items [a, b).
+long long items_of(const PairShape &sh, const std::vector<int> &act_sizes) {
+    long long t = 0;
+    for (int n : act_sizes)
+        if (n > 0) t += (long long)ceil_div(n, itile_for(sh.R, lanes_for(sh, n))) * ceil_div(n, sh.jchunk);
+    return t;
+}
+double pairs_of_items(const PairShape &sh, const std::vector<int> &act_sizes, long long a, long long b) {
+    double pairs = 0.0;
+    long long base = 0;
+    for (int n : act_sizes) {
+        if (n <= 0) continue;
+        const int itile = itile_for(sh.R, lanes_for(sh, n));
+        const int js = ceil_div(n, sh.jchunk);
+        const long long cnt = (long long)ceil_div(n, itile) * js;
+        for (long long it = std::max(a, base); it < std::min(b, base + cnt); ++it) {
+            const long long local = it - base;
+            const int ti = (int)(local / js), jc = (int)(local % js);
+            pairs += (double)std::min(itile, n - ti * itile) * (double)std::min(sh.jchunk, n - jc * sh.jchunk);
+        }
+        base += cnt;
+        if (base >= b) break;
+    }
+    return pairs;
+}
+
+// Pair terms per second of shape sh, timed on up to three windows of its work
+// items (near the start, the middle and the end of the item range, so that
+// large and small events are both sampled); 0 if the shape is not usable.
+gc_status time_shape(gc_sim *s, const PairShape &sh, const std::vector<int> &act_sizes, cudaEvent_t ea,
+                     cudaEvent_t eb, double *rate) {
+    *rate = 0.0;
+    if (sh.n_blocks <= 0) return GC_OK;
+    long long n_max = 1;
+    for (int n : act_sizes) n_max = std::max<long long>(n_max, n);
+    if ((n_max + sh.jchunk - 1) / sh.jchunk > s->part_cap_chunks) return GC_OK;
+    const long long items = items_of(sh, act_sizes);
+    if (items <= 0) return GC_OK;
+    const long long K = std::min<long long>(items, 2LL * sh.n_blocks);  // two waves per window
+    double total_pairs = 0.0;
+    for (int n : act_sizes) total_pairs += (double)n * (double)n;
+    std::vector<long long> starts;
+    // whole launches while they are short (~30 ms): they include the tail of
+    // a launch and the real mix of event sizes; sampled windows beyond that
+    if (items <= 3 * K || total_pairs < 1e11) starts = {0};
+    else if (act_sizes.size() == 1) starts = {(items - K) / 2};  // one event: uniform items
+    else for (double f : {0.05, 0.5, 0.9}) starts.push_back(std::min(items - K, (long long)(f * items)));
+    const long long len = starts.size() == 1 && starts[0] == 0 ? items : K;
+    s->dev.shape = sh;
+    GC_CUDA(launch_build_items(s->dev, s->stream));
+    double pairs = 0.0, secs = 0.0;
+    for (long long st : starts) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {  // the first launch warms up; short windows are repeated
+            if (rep >= 2 && best > 2.0f) break;
+            s->h_probe[0] = (unsigned)(st + len);  // items_total, then work_counter
+            s->h_probe[1] = (unsigned)st;
+            GC_CUDA(cudaMemcpyAsync(&s->dev.ctrl->items_total, s->h_probe, 2 * sizeof(unsigned),
+                                    cudaMemcpyHostToDevice, s->stream));
+            GC_CUDA(cudaEventRecord(ea, s->stream));
+            GC_CUDA(launch_pair(s->dev, s->p.precision, s->p.newton, s->stream));
+            GC_CUDA(cudaEventRecord(eb, s->stream));
+            GC_CUDA(cudaEventSynchronize(eb));
+            float ms = 0.f;
+            GC_CUDA(cudaEventElapsedTime(&ms, ea, eb));
+            if (rep > 0) best = std::min(best, ms);
+        }
+        pairs += pairs_of_items(sh, act_sizes, st, st + len);
+        secs += best * 1e-3;
+    }
+    *rate = secs > 0 ? pairs / secs : 0.0;
+    ++s->tune_candidates;
+    return GC_OK;
+}
+
+// Pick the FP32 pair kernel's knobs.  autotune = 0: the default knobs (R = 4
+// or pair_R).  autotune = 1: the cached choice for this device, form and
+// workload histogram, else a staged search timed on the loaded carriers:
+// R x V, then blocks per SM, then the j-chunk target, then (when some events
+// lie between 1024 and 4096 holes) the 4-lane threshold.
 gc_status choose_shape(gc_sim *s, const std::vector<long long> &sizes) {
-    PairShape best = s->dev.shape;
+    s->tune_ms = 0.0;
+    s->tune_candidates = 0;
+    s->tune_cached = 0;
     if (fp64_mode(s)) {
         s->dev.shape = fp64_shape(s->sm_count, sizes, s->p.jchunk, s->part_cap_chunks);
         GC_CUDA(launch_build_items(s->dev, s->stream));
         return GC_OK;
     }
-    int cands[3] = {2, 4, 8};
-    float best_ms = 1e30f;
-    bool tune = s->p.autotune && s->phys.coulomb && s->n > 0 && s->p.pair_R == 0;
-    int first = tune ? 0 : 1, last = tune ? 2 : 1;
-    if (s->p.pair_R != 0) cands[1] = s->p.pair_R;
-    cudaEvent_t a = nullptr, b = nullptr;
+    long long n_max = 1;
+    for (long long n : sizes) n_max = std::max(n_max, n);
+    TuneKnobs def;
+    if (s->p.pair_R) def.R = s->p.pair_R;
+    const bool tune = s->p.autotune && s->phys.coulomb && s->n > 0;
+    auto fits = [&](const PairShape &sh) {
+        return sh.n_blocks > 0 && (n_max + sh.jchunk - 1) / sh.jchunk <= s->part_cap_chunks;
+    };
+    TuneKnobs best = def;
+    if (!fits(shape_of(s, sizes, best)))  // the default does not fit the partial buffer: try the others
+        for (int R : {2, 4, 8}) {
+            TuneKnobs k = def;
+            k.R = s->p.pair_R ? s->p.pair_R : R;
+            if (fits(shape_of(s, sizes, k))) {
+                best = k;
+                break;
+            }
+        }
     if (tune) {
-        GC_CUDA(cudaEventCreate(&a));
-        GC_CUDA(cudaEventCreate(&b));
+        const std::string key = tune_key(s, sizes);
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                best = it->second;
+                hit = true;
+            }
+        }
+        if (hit && fits(shape_of(s, sizes, best))) {
+            s->tune_cached = 1;
+        } else {
+            const auto t0 = std::chrono::steady_clock::now();
+            // active sizes after the step-0 pass, in internal event order
+            std::vector<int> off(s->E + 1), act(s->E);
+            GC_CUDA(cudaMemcpyAsync(off.data(), s->dev.ev_off[s->h_ctrl->cur], (s->E + 1) * sizeof(int),
+                                    cudaMemcpyDeviceToHost, s->stream));
+            GC_CUDA(cudaStreamSynchronize(s->stream));
+            for (int64_t e = 0; e < s->E; ++e) act[e] = off[e + 1] - off[e];
+            cudaEvent_t ea = nullptr, eb = nullptr;
+            GC_CUDA(cudaEventCreate(&ea));
+            GC_CUDA(cudaEventCreate(&eb));
+            double best_rate = 0.0;
+            gc_status st = GC_OK;
+            auto trial = [&](const TuneKnobs &k) {
+                if (st != GC_OK) return;
+                double r = 0.0;
+                st = time_shape(s, shape_of(s, sizes, k), act, ea, eb, &r);
+                if (st == GC_OK && r > best_rate) {
+                    best_rate = r;
+                    best = k;
+                }
+            };
+            for (int R : {2, 4, 8}) {  // stage 1: R x V
+                if (s->p.pair_R && R != s->p.pair_R) continue;
+                for (int V : {0, 1, 2}) {
+                    TuneKnobs k = def;
+                    k.R = R;
+                    k.V = V;
+                    trial(k);
+                }
+            }
+            const TuneKnobs b1 = best;  // stage 2: fewer resident blocks per SM
+            const int occ = pair_kernel_occupancy(s->p.precision, b1.R, s->p.newton, s->dev.tile_frames, b1.V);
+            for (int bps = 1; bps < occ; ++bps) {
+                TuneKnobs k = b1;
+                k.bps = bps;
+                trial(k);
+            }
+            if (!s->p.jchunk) {  // stage 3: j-chunk target
+                const TuneKnobs b2 = best;
+                for (int t : {16, 64}) {
+                    TuneKnobs k = b2;
+                    k.target = t;
+                    trial(k);
+                }
+            }
+            bool mid = false;  // stage 4: the 4-lane threshold, if it matters here
+            for (int n : act) mid = mid || (n >= 1024 && n < 4096);
+            if (mid) {
+                const TuneKnobs b3 = best;
+                for (int sn : {1024, 4096}) {
+                    TuneKnobs k = b3;
+                    k.small_n = sn;
+                    trial(k);
+                }
+            }
+            cudaEventDestroy(ea);
+            cudaEventDestroy(eb);
+            if (st != GC_OK) return st;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                g_tune_cache[key] = best;
+            }
+            s->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
     }
-    for (int ci = first; ci <= last; ++ci) {
-        PairShape sh = fp32_shape(cands[ci], s->sm_count, s->p.precision, s->p.newton, s->dev.tile_frames);
-        sh.jchunk = choose_jchunk(sizes, sh, s->p.jchunk, kTileJ);
-        long long n_max = 1;
-        for (long long n : sizes) n_max = std::max(n_max, n);
-        if ((n_max + sh.jchunk - 1) / sh.jchunk > s->part_cap_chunks) continue;
-        if (!tune) {
-            best = sh;
-            break;
-        }
-        s->dev.shape = sh;
-        GC_CUDA(launch_build_items(s->dev, s->stream));
-        float ms_best = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {
-            GC_CUDA(cudaMemsetAsync(&s->dev.ctrl->work_counter, 0, sizeof(unsigned), s->stream));
-            GC_CUDA(cudaEventRecord(a, s->stream));
-            GC_CUDA(launch_pair(s->dev, s->p.precision, s->p.newton, s->stream));
-            GC_CUDA(cudaEventRecord(b, s->stream));
-            GC_CUDA(cudaEventSynchronize(b));
-            float ms = 0.f;
-            GC_CUDA(cudaEventElapsedTime(&ms, a, b));
-            if (rep > 0) ms_best = std::min(ms_best, ms);  // the first launch warms up
-        }
-        if (ms_best < best_ms) {
-            best_ms = ms_best;
-            best = sh;
-        }
-    }
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
-    s->dev.shape = best;
+    s->dev.shape = shape_of(s, sizes, best);
     GC_CUDA(launch_build_items(s->dev, s->stream));
     return GC_OK;
 }
@@ -572,6 +779,7 @@ gc_status gc_create(const gc_params *p, void *cuda_stream, gc_sim **out) {
         }
         if ((e = cudaMallocHost((void **)&s->h_ctrl, sizeof(Ctrl))) != cudaSuccess) { st = cuda_fail(e); break; }
         if ((e = cudaMallocHost((void **)&s->h_limit, 2 * sizeof(long long))) != cudaSuccess) { st = cuda_fail(e); break; }
+        if ((e = cudaMallocHost((void **)&s->h_probe, 2 * sizeof(unsigned))) != cudaSuccess) { st = cuda_fail(e); break; }
         std::memset(s->h_ctrl, 0, sizeof(Ctrl));
     } while (0);
     if (st != GC_OK) {
@@ -676,11 +884,13 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         const PairShape sh = fp64_shape(s->sm_count, sizes, s->p.jchunk, 0);
         cap = (n_max + sh.jchunk - 1) / sh.jchunk;
     } else if (s->phys.coulomb) {
-        for (int R : {2, 4, 8}) {
-            const PairShape sh = fp32_shape(R, s->sm_count, s->p.precision, s->p.newton, frames);
-            const int jc = choose_jchunk(sizes, sh, s->p.jchunk, kTileJ);
-            cap = std::max(cap, (n_max + jc - 1) / jc);
-        }
+        for (int R : {2, 4, 8})  // every j-chunk the autotuner may try (up to 64 items per block)
+            for (int target : {32, 64}) {
+                PairShape sh = fp32_shape(R, s->sm_count, s->p.precision, s->p.newton, frames);
+                sh.n_blocks = sh.n_blocks * target / 32;
+                const int jc = choose_jchunk(sizes, sh, s->p.jchunk, kTileJ);
+                cap = std::max(cap, (n_max + jc - 1) / jc);
+            }
     }
     s->part_cap_chunks = cap;
 
@@ -1043,6 +1253,11 @@ gc_status gc_get_stats(gc_sim *s, gc_stats *out) {
     out->timed_steps = s->timed_steps;
     out->device_loop = use_graph(s) && (!s->graph || s->graph_loops) && (!s->graph_small || s->small_loops);
     out->fused_path = s->fused_ran;
+    out->tune_ms = s->tune_ms;
+    out->tune_candidates = s->tune_candidates;
+    out->tune_cached = s->tune_cached;
+    out->pair_kernel_variant = s->dev.shape.V;
+    out->small_n = s->dev.shape.small_n;
     return GC_OK;
 }
 
@@ -1220,6 +1435,7 @@ void gc_destroy(gc_sim *s) {
     free_state(s);
     if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
     if (s->h_limit) cudaFreeHost(s->h_limit);
+    if (s->h_probe) cudaFreeHost(s->h_probe);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }

@@ -82,6 +82,7 @@ struct PairShape {
     int small_n;     // events with fewer active carriers use small_lanes lanes per i-group
     int small_lanes; // lanes per i-group of small events: 4 (FP32 forms) or 16 (FP64 form)
     int n_blocks;    // persistent grid size
+    int V;           // pair-kernel variant chosen by the autotuner (0 = default)
 };
 
 // Device view of a simulation, passed by value to every kernel.

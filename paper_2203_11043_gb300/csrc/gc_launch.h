@@ -25,8 +25,9 @@ PairShape field_shape(int precision, int sm_count, long long n, long long max_ch
 
 // Pair kernel (Eq. 6): precision 0 = FP64 form, 1 = FP32, 2 = FP32 + Kahan,
 // 3 = FP16x2; tile_frames != 0 selects the FP32 forms' tile-frame variant.
-const void *pair_kernel_ptr(int precision, int R, int newton, int tile_frames);
-int pair_kernel_occupancy(int precision, int R, int newton, int tile_frames);
+// V: the autotuner's kernel variant (see pair_min_blocks).
+const void *pair_kernel_ptr(int precision, int R, int newton, int tile_frames, int V = 0);
+int pair_kernel_occupancy(int precision, int R, int newton, int tile_frames, int V = 0);
 cudaError_t launch_pair(const Dev &d, int precision, int newton, cudaStream_t st);
 
 // One time step after the pair sum: integrate (mobility, drift, diffusion,

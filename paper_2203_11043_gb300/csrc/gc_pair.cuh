@@ -57,7 +57,9 @@ namespace gc {
 // LIST (the persistent single-event kernel): the event's shadow `shb` is
 // indexed by hole id, list[slot] in shared memory; otherwise shb = sh32 +
 // e_start is indexed by slot.
-template <int R, bool KAHAN, bool NEWTON, int L, bool H16, bool TF, bool LIST = false>
+// JUH (one lane per i-group only): 1 halves the 16-byte loads in flight per
+// coordinate (an autotuner variant; the per-carrier sum order is unchanged).
+template <int R, bool KAHAN, bool NEWTON, int L, bool H16, bool TF, bool LIST = false, int JUH = 0>
 __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int n_e, int local,
                                                  float scale, float *__restrict__ sx,
                                                  float *__restrict__ sy, float *__restrict__ sz,
@@ -76,7 +78,8 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
     // 16-byte loads (4 j's) per coordinate per iteration: about 16 packed
     // pair chains in flight per lane (R * JU * 2 = 16 on one lane; the 4-lane
     // path measured best at 4 for R = 2, against 2 and 8)
-    constexpr int JU = L == 1 ? (R >= 8 ? 1 : 8 / R) : 4;
+    constexpr int JU0 = L == 1 ? (R >= 8 ? 1 : 8 / R) : 4;
+    constexpr int JU = (L == 1 && JUH) ? (JU0 > 1 ? JU0 / 2 : 1) : JU0;
     constexpr int STEP = 4 * JU * L;  // j's consumed per unrolled iteration by the L lanes
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane / L, ph = lane % L;
@@ -327,8 +330,14 @@ __device__ __forceinline__ int event_of_item(const int *__restrict__ base, int n
 // after each item, the item that completes its i-tile's j-chunks integrates
 // that i-tile (fused_tile_done), so one launch does the pair sum and the
 // per-carrier step; the one-block small_tail kernel then compacts.
-template <int R, bool KAHAN, bool NEWTON, bool H16, bool TF, bool FUSED>
-__global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
+// Autotuner variants V of the unfused FP32 kernel (the arithmetic per carrier
+// is the same in all of them, so they give the same bits): 0 = the default;
+// 1 = half the loads in flight on one lane; 2 = a register budget for one
+// more resident block per SM (4 at R = 2, 3 at R = 4).
+__host__ __device__ constexpr int pair_min_blocks(int R, int V) { return V == 2 ? (R == 2 ? 4 : 3) : 1; }
+
+template <int R, bool KAHAN, bool NEWTON, bool H16, bool TF, bool FUSED, int V = 0>
+__global__ void __launch_bounds__(kPairThreads, pair_min_blocks(R, V)) pair_fp32_kernel(Dev d) {
     __shared__ __align__(16) float s_x[4 * kTileJ], s_y[4 * kTileJ], s_z[4 * kTileJ];
     __shared__ float4 s_fr[TF ? 6 : 1];  // tile frames: the item frame, then two j-tile frames
     __shared__ __align__(16) float4 s_raw[4 * kTileJ];  // cp.async landing slots of the next j-tile
@@ -349,8 +358,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_fp32_kernel(Dev d) {
         const int local = item - d.item_base[e];
         const float scale = H16 ? h2_scale(__uint_as_float(ext[e])) : 1.0f;
         if (lanes_for(d.shape, n_e) == 1)
-            pair_item_fp32_j<R, KAHAN, NEWTON, 1, H16, TF>(d, e_start, n_e, local, scale, s_x, s_y,
-                                                           s_z, s_fr, s_raw, d.sh32 + e_start);
+            pair_item_fp32_j<R, KAHAN, NEWTON, 1, H16, TF, false, V == 1>(d, e_start, n_e, local, scale, s_x,
+                                                                          s_y, s_z, s_fr, s_raw, d.sh32 + e_start);
         else
             pair_item_fp32_j<R, KAHAN, NEWTON, 4, H16, false>(d, e_start, n_e, local, scale, s_x, s_y,
                                                               s_z, s_fr, s_raw, d.sh32 + e_start);

@@ -80,6 +80,11 @@ class GcStats(ctypes.Structure):
         ("timed_steps", ctypes.c_int64),
         ("device_loop", ctypes.c_int32),
         ("fused_path", ctypes.c_int32),
+        ("tune_ms", ctypes.c_double),
+        ("tune_candidates", ctypes.c_int32),
+        ("tune_cached", ctypes.c_int32),
+        ("pair_kernel_variant", ctypes.c_int32),
+        ("small_n", ctypes.c_int32),
     ]
 
 

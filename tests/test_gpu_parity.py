@@ -577,3 +577,45 @@ def test_fused_takes_over_below_its_limit(gc):
         assert a["stats"]["fused_path"] == 0 and b["stats"]["fused_path"] == path
         assert_same_run(a, b)
         assert b["status"] == 0 and b["stats"]["n_active"] == 0
+
+
+# ---- autotuner ------------------------------------------------------------------------------------
+
+def test_autotuner_searches_caches_and_stays_within_bound(gc):
+    """autotune = 1 times candidate shapes (carriers per thread, kernel variant,
+    blocks per SM, j-chunk, 4-lane threshold) on sampled work items, caches
+    the choice for the same device, form and workload histogram, and the
+    chosen shape's step agrees with the oracle's step."""
+    wl = I.single_cloud(n=20000, sigma_um=0.6, z0_um=150.0, seed=61, img=32)
+    shapes = []
+    for _ in range(2):
+        p = gc.gc_default_params(precision=2, img_w=32, img_h=32, fuse_small=0)
+        with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+            st = sim.stats()
+            x0 = sim.positions()
+            sim.run(1)
+            x1 = sim.positions()
+        shapes.append(st)
+    first, second = shapes
+    assert first["tune_cached"] == 0 and first["tune_candidates"] >= 4 and first["tune_ms"] > 0
+    assert second["tune_cached"] == 1 and second["tune_candidates"] == 0
+    for k in ("pair_variant", "pair_kernel_variant", "pair_blocks", "jchunk", "small_n"):
+        assert first[k] == second[k], k
+    rng = np.random.default_rng(5)
+    tg = np.sort(rng.choice(wl.n, size=64, replace=False))
+    want = O.step_targets(O.make_params(img_w=32, img_h=32), x0, np.arange(wl.n), tg, int(wl.seeds[0]), 1)
+    assert np.abs(x1[tg] - want).max() < 1e-4
+
+
+def test_pair_shape_knobs_do_not_change_results(gc):
+    """Carriers per thread (and so the i-tile) do not change the per-carrier
+    sum order: with the j-chunk fixed, every R gives the same bits."""
+    wl = I.single_cloud(n=6000, sigma_um=0.5, z0_um=100.0, seed=62, img=32)
+    outs = []
+    for R in (2, 4, 8):
+        p = gc.gc_default_params(precision=2, img_w=32, img_h=32, autotune=0, pair_R=R, jchunk=1024,
+                                 fuse_small=0)
+        with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+            sim.run(3)
+            outs.append(sim.positions())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])

@@ -126,7 +126,7 @@ def test_batch_with_one_large_event(gc):
     res = []
     for tf in (0, 1):
         p = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=img, img_h=img, pair_R=4,
-                                 jchunk=8192, tile_frames=tf)
+                                 jchunk=8192, tile_frames=tf, autotune=0)  # the same shape in both frames
         with gc.Simulation(p, xyz, ev_off, seeds, origin) as sim:
             st, steps = sim.run(-1)
             assert st == gc.GC_OK

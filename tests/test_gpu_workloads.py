@@ -57,7 +57,7 @@ def assert_statistics(pos_a, pos_b, img_a, img_b, n):
 @pytest.fixture(scope="module")
 def batch(gc):
     wl = I.xray_batch(n_events=512)
-    return wl, run(gc, wl, gc.GC_FP32_KAHAN, pair_R=4, jchunk=8192)
+    return wl, run(gc, wl, gc.GC_FP32_KAHAN, pair_R=4, jchunk=8192, autotune=0)
 
 
 def test_batch_counts_exact(gc, batch):
@@ -100,12 +100,14 @@ def test_batch_events_against_oracle(gc, batch):
 
 
 def test_batched_equals_per_event(gc, batch):
-    """An event inside the batch is bit-identical to the same event alone."""
+    """An event inside the batch is bit-identical to the same event alone
+    (with the pair shape pinned: the autotuner may choose a different 4-lane
+    threshold or j-chunk for a different workload)."""
     wl, res = batch
     sizes = np.diff(wl.ev_off)
     for e in [int(np.argmin(sizes)), 7, int(np.argmax(sizes))]:
         ev = event_slice(wl, e)
-        alone = run(gc, ev, gc.GC_FP32_KAHAN, pair_R=4, jchunk=8192)
+        alone = run(gc, ev, gc.GC_FP32_KAHAN, pair_R=4, jchunk=8192, autotune=0)
         a, b = int(wl.ev_off[e]), int(wl.ev_off[e + 1])
         assert np.array_equal(alone["positions"], res["positions"][a:b])
         assert np.array_equal(alone["collect_step"], res["collect_step"][a:b])
