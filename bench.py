@@ -441,12 +441,24 @@ def main():
     stream = torch.cuda.current_stream()
     sms, ccmaj, ccmin = gc.gc_device_info()
 
-    wl = make_workload(args.workload)
-    if args.n_carriers:
-        wl = inputs.subsample(wl, args.n_carriers, seed=3)
-    # every rank runs an independent replica of the event (replicas only: the
-    # single event is not sharded); seeds differ per rank
-    seeds = replica_seeds(wl.seeds, rank)
+    if args.workload == "xray-batch" and world > 1:
+        # sharded: a global batch of 4096 events per rank, dealt by LPT on
+        # N^2 (z0 + 5 um); each rank loads and runs only its events, with no
+        # collective in the run (weak scaling: per-rank work fixed)
+        from paper_2203_11043_gb300 import shard
+        glob = inputs.xray_batch(n_events=4096 * world)
+        wl = shard.sub_workload(glob, shard.lpt_partition(shard.event_costs(glob), world)[rank])
+        seeds = wl.seeds
+        parallelism = f"events sharded x{world} (LPT on N^2 (z0 + 5 um), {glob.n_events} events in all)"
+    else:
+        wl = make_workload(args.workload)
+        if args.n_carriers:
+            wl = inputs.subsample(wl, args.n_carriers, seed=3)
+        # every rank runs an independent replica of the workload (its seeds
+        # differ per rank): one event is not split across GPUs
+        seeds = replica_seeds(wl.seeds, rank)
+        parallelism = f"replicas x{world}"
+
     params = gc.gc_default_params(precision=gc.GC_FP32_KAHAN, img_w=wl.img_w, img_h=wl.img_h,
                                   graph_steps=1, timing=1, pair_R=args.pair_R, coulomb=args.coulomb,
                                   tile_frames=args.tile_frames)
@@ -514,7 +526,7 @@ def main():
                                  else "event centroid",
                        "pair_R": after["pair_variant"], "pair_blocks": after["pair_blocks"],
                        "jchunk": after["jchunk"], "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": f"replicas x{world}", "device": f"sm_{ccmaj}{ccmin}, {sms} SMs"},
+                       "parallelism": parallelism, "device": f"sm_{ccmaj}{ccmin}, {sms} SMs"},
             "carrier_steps_per_s": csteps / (total_ms / 1e3), "steps_done": steps_done,
             "roofline": roofline, "gpu_launches": int(steps_done * after["launches_per_step"]),
             "clocks": clocks}

@@ -42,7 +42,10 @@ typedef enum {
     GC_ERR_CUDA = -3,            /* a CUDA runtime call failed (see gc_last_cuda_error) */
     GC_ERR_STATE = -4,           /* call out of order (e.g. gc_run before gc_load_carriers) */
     GC_ERR_DEVICE_TIMEOUT = -5,  /* a bounded device-side wait expired; state is undefined */
-    GC_ERR_NO_DEVICE = -6        /* no CUDA device available */
+    GC_ERR_NO_DEVICE = -6,       /* no CUDA device available */
+    GC_ERR_DEVICE_CHECK = -7     /* a device-side consistency check failed (event offsets; in
+                                    GC_DEBUG builds also slot, pixel and partial-sum indices);
+                                    the access was skipped, state is undefined */
 } gc_status;
 
 /* Arithmetic of the Eq. 6 pair sum.  Positions, the pixel-boundary test and
@@ -253,6 +256,14 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
 gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, double softening_um,
                                    double eps_si_rel, int32_t precision, double *E_dev,
                                    void *cuda_stream);
+
+/* Fault planting for tests of the device-side checks (no counterpart in the
+ * paper), effective only in builds compiled with GC_DEBUG (GC_ERR_STATE
+ * otherwise): what = 1 makes the next gc_load_carriers of `s` upload event
+ * offsets that do not match its carriers.  The load then succeeds, no kernel
+ * uses the offsets (the step-0 pass checks them first), and gc_run returns
+ * GC_ERR_DEVICE_CHECK.  what = 0 cancels. */
+gc_status gc_debug_inject(gc_sim *s, int32_t what);
 
 /* Self-test of the library's bounded device-side wait (the grid barrier of
  * the persistent single-event kernel; no counterpart in the paper): runs, on

@@ -210,6 +210,8 @@ struct gc_sim {
     bool se_ok = false;              // the persistent single-event kernel applies
     int se_grid = 0;
     unsigned *h_probe = nullptr;     // pinned: items_total, work_counter of an autotuner probe
+    int device_error = 0;            // Ctrl::error bits seen after the last load or run
+    int inject = 0;                  // GC_DEBUG builds: fault to plant at the next load (gc_debug_inject)
     double tune_ms = 0.0;            // autotuner: host time spent at the last load
     int tune_candidates = 0;         //   shapes timed
     int tune_cached = 0;             //   1: the shape came from the in-process cache
@@ -229,6 +231,12 @@ struct gc_sim {
 namespace {
 
 bool fp64_mode(const gc_sim *s) { return s->p.precision == GC_FP64; }
+
+// The status of a failed device-side check (Ctrl::error bits); the state of
+// the simulation is undefined afterwards.
+gc_status device_error_status(int bits) {
+    return (bits & kErrBarrierTimeout) ? GC_ERR_DEVICE_TIMEOUT : GC_ERR_DEVICE_CHECK;
+}
 // Timing mode launches eagerly: events recorded by captured graph nodes
 // cannot be used with cudaEventElapsedTime.
 bool use_graph(const gc_sim *s) { return s->p.graph_steps > 0 && !s->p.timing; }
@@ -716,6 +724,7 @@ const char *gc_status_string(gc_status st) {
         case GC_ERR_STATE: return "GC_ERR_STATE: call out of order";
         case GC_ERR_DEVICE_TIMEOUT: return "GC_ERR_DEVICE_TIMEOUT: bounded device wait expired";
         case GC_ERR_NO_DEVICE: return "GC_ERR_NO_DEVICE: no CUDA device";
+        case GC_ERR_DEVICE_CHECK: return "GC_ERR_DEVICE_CHECK: a device-side consistency check failed";
     }
     return "unknown gc_status";
 }
@@ -857,6 +866,10 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
         }
     }
     ioff[E] = pos;
+#ifdef GC_DEBUG
+    if (s->inject == 1) ioff[E] = pos + 7;  // planted: the offsets no longer match the carriers
+    s->inject = 0;
+#endif
     // tile frames (FP32 forms, on request, when some event has >= small_n
     // holes): the large events in spatial (Morton) order
     const int small_n = kSmallEvent;
@@ -1021,6 +1034,11 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     GC_CUDA(cudaStreamSynchronize(st));
     gc_status r = read_ctrl(s);
     if (r != GC_OK) return r;
+    s->device_error = s->h_ctrl->error;
+    if (s->device_error) {  // the step-0 pass found the input inconsistent: gc_run reports it
+        s->loaded = true;
+        return GC_OK;
+    }
     if (s->phys.coulomb && n > 0) {
         r = choose_shape(s, sizes);  // the sizes the partial buffer was sized for
         if (r != GC_OK) return r;
@@ -1060,6 +1078,7 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
     if (steps_done) *steps_done = 0;
     if (!s) return GC_ERR_PARAM;
     if (!s->loaded) return GC_ERR_STATE;
+    if (s->device_error) return device_error_status(s->device_error);
     GC_CUDA(cudaSetDevice(s->device));
     const long long step0 = s->h_ctrl->step;
     const long long max_steps = s->p.max_steps;
@@ -1085,9 +1104,9 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
                 GC_CUDA(launch_se_loop(s->dev, s->p.precision, grid, kDeviceWaitLimitS, s->stream));
                 r = read_ctrl(s);
                 if (r != GC_OK) return r;
-                if (s->h_ctrl->error) {
-                    s->loaded = false;  // the state is undefined after a wait ran out
-                    return GC_ERR_DEVICE_TIMEOUT;
+                if (s->h_ctrl->error) {  // the state is undefined after a failed check or wait
+                    s->device_error = s->h_ctrl->error;
+                    return device_error_status(s->device_error);
                 }
                 GC_CUDA(launch_build_items(s->dev, s->stream));  // items in the other paths' layout
                 break;
@@ -1158,6 +1177,10 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
             }
             if (fz || s->h_ctrl->n_active <= 0 || s->h_ctrl->step >= limit) break;
             if (!(s->fused_ok && s->h_ctrl->n_active <= kFusedMax)) break;
+        }
+        if (s->h_ctrl->error) {
+            s->device_error = s->h_ctrl->error;
+            return device_error_status(s->device_error);
         }
         r = set_limit(s, s->h_ctrl->step);  // closed until the next gc_run
         if (r != GC_OK) return r;
@@ -1409,6 +1432,16 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
     cudaStreamSynchronize(st);
     m.release();
     return status;
+}
+
+gc_status gc_debug_inject(gc_sim *s, int32_t what) {
+    if (!s || what < 0 || what > 1) return GC_ERR_PARAM;
+#ifdef GC_DEBUG
+    s->inject = what;
+    return GC_OK;
+#else
+    return GC_ERR_STATE;  // only builds with GC_DEBUG plant faults
+#endif
 }
 
 gc_status gc_selftest_barrier_timeout(double limit_s) {

@@ -12,8 +12,6 @@
 
 namespace gc {
 
-constexpr int kErrBarrierTimeout = 1;  // Ctrl::error bit: a grid barrier wait ran out
-
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -147,10 +147,29 @@ __host__ __device__ inline int lanes_for(const PairShape &sh, int n) { return n 
 __host__ __device__ inline int itile_for(int R, int lanes) { return R * kPairThreads / lanes; }
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-// A step is skipped when the run limit is reached or nothing is active.
+// Ctrl::error bits (the host maps them to a status after each run).
+constexpr int kErrBarrierTimeout = 1;  // a grid-barrier wait ran out
+constexpr int kErrOffsets = 2;         // the active event offsets are inconsistent
+constexpr int kErrIndex = 4;           // a GC_DEBUG bounds check failed (the access was skipped)
+
+// A step is skipped when the run limit is reached, nothing is active, or a
+// device-side check has failed (no kernel then uses the state again).
 __device__ inline bool step_skipped(const Ctrl *c) {
-    return c->step >= c->step_limit || c->n_active <= 0;
+    return c->step >= c->step_limit || c->n_active <= 0 || c->error != 0;
 }
+
+// GC_DEBUG builds check the index behind each data-dependent access: a failed
+// check sets kErrIndex and the access is skipped (never a trap).  Release
+// builds compile the checks away.
+__device__ __forceinline__ bool guard_ok(bool ok, Ctrl *c) {
+    if (!ok) atomicOr(&c->error, kErrIndex);
+    return ok;
+}
+#ifdef GC_DEBUG
+#define GC_GUARD(cond) (::gc::guard_ok((cond), d.ctrl))
+#else
+#define GC_GUARD(cond) (true)
+#endif
 
 // ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------------
 // Ten rounds of the 4x32 Philox S-box with multipliers 0xD2511F53 and

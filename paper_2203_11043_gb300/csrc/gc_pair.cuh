@@ -267,7 +267,7 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
             for (int o = 1; o < L; o <<= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
         }
         const int il = il0 + r * STRIDE;
-        if (ph == 0 && il < n_e) {
+        if (ph == 0 && il < n_e && GC_GUARD(e_start + il < d.n_total)) {
             const long long p = e_start + il;
             P[p] = v[0];
             P[d.part_stride + p] = v[1];
@@ -425,7 +425,7 @@ __device__ __forceinline__ void pair_item_fp64(const Dev &d, int e_start, int n_
         ey += __shfl_xor_sync(0xffffffffu, ey, o);
         ez += __shfl_xor_sync(0xffffffffu, ez, o);
     }
-    if (ph == 0 && il < n_e) {
+    if (ph == 0 && il < n_e && GC_GUARD(e_start + il < d.n_total)) {
         double *P = d.partial + (long long)jc * 3 * d.part_stride;
         const long long p = e_start + il;
         P[p] = ex;

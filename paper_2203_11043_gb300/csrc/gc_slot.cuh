@@ -143,6 +143,7 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
         if (ph.coulomb) {  // Eq. 6: sum of the per-chunk partial sums, fixed order
             const int js = ceil_div(n_e, d.shape.jchunk);
             const long long st = d.part_stride;
+            if (!GC_GUARD(p >= 0 && p < d.n_total)) return false;
             const double *P = d.partial + p;
             // loads of up to 8 chunks are issued before their (ordered) sums,
             // so the chunk count does not chain memory round trips
@@ -245,8 +246,10 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
         const double fy = floor((y - d.img_origin[2 * e + 1]) / ph.pixel);
         if (fx >= 0.0 && fx < (double)ph.img_w && fy >= 0.0 && fy < (double)ph.img_h) {
             const long long pix = ((long long)eu * ph.img_h + (long long)fy) * ph.img_w + (long long)fx;
-            atomicAdd(&d.image[pix], 1u);
-        } else {
+            if (GC_GUARD(eu >= 0 && eu < d.n_events && pix >= 0 &&
+                         pix < (long long)d.n_events * ph.img_h * ph.img_w))
+                atomicAdd(&d.image[pix], 1u);
+        } else if (GC_GUARD(eu >= 0 && eu < d.n_events)) {
             atomicAdd(&d.off_image[eu], 1ull);
         }
         atomicAdd(&d.ev_collected_now[e], 1);

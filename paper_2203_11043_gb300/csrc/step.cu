@@ -34,7 +34,7 @@ namespace gc {
 __global__ void __launch_bounds__(256) shadow_kernel(Dev d) {
     Ctrl *c = d.ctrl;
     const int n = c->n_active;
-    if (n <= 0) return;
+    if (n <= 0 || c->error) return;
     const int cur = c->cur;
     const int *act = d.act[cur];
     const int *off = d.ev_off[cur];
@@ -240,9 +240,13 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
             const bool keep = (w >> lane) & 1u;
             int e = -1;
             unsigned ext_bits = 0u;
-            if (keep) {
-                const int q = base + s_wpre[m] + __popc(w & ((1u << lane) - 1u));
-                const int id = src[p];
+            // ok: kept and (GC_DEBUG) its slot, target slot and id in range;
+            // every lane still reaches the warp-wide vote below
+            bool ok = keep && GC_GUARD(p < d.n_total);
+            const int q = base + s_wpre[m] + __popc(w & ((1u << lane) - 1u));
+            const int id = ok ? src[p] : 0;
+            ok = ok && GC_GUARD(q >= 0 && q < d.n_total && id >= 0 && id < d.n_total);
+            if (ok) {
                 dst[q] = id;
                 // the shadow in the event frame (with tile frames the FP32 shadow
                 // is written by shadow_kernel once the new event offsets are known)
@@ -262,13 +266,13 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
             }
             if (!F64 && !d.tile_frames && d.ev_ext[0] && (d.phys.coulomb || d.phys.stored)) {
                 unsigned *ext = d.ev_ext[cur ^ 1];  // FP16x2: max |coordinate|, warp-aggregated
-                const unsigned lead = __ffs(__ballot_sync(0xffffffffu, keep));
+                const unsigned lead = __ffs(__ballot_sync(0xffffffffu, ok));
                 if (lead) {
                     const int e0 = __shfl_sync(0xffffffffu, e, lead - 1);
-                    if (__all_sync(0xffffffffu, !keep || e == e0)) {
+                    if (__all_sync(0xffffffffu, !ok || e == e0)) {
                         const unsigned mx = __reduce_max_sync(0xffffffffu, ext_bits);
                         if (lane == 0) atomicMax(&ext[e0], mx);
-                    } else if (keep) {
+                    } else if (ok) {
                         atomicMax(&ext[e], ext_bits);
                     }
                 }
@@ -298,6 +302,22 @@ __device__ __forceinline__ void finalize_block(const Dev &d, long long *s_warp) 
     const int cur = c->cur;
     const int *off = d.ev_off[cur];
     int *noff = d.ev_off[cur ^ 1];
+    // The active event offsets (and this step's collections) must be
+    // consistent before they size anything: otherwise flag kErrOffsets and
+    // leave the state alone; every later kernel then skips its step.
+    {
+        int bad = 0;
+        for (int e = threadIdx.x; e < d.n_events; e += blockDim.x) {
+            const int a = off[e], b = off[e + 1];
+            const int k = d.ev_collected_now[e];
+            if (a < 0 || b < a || b > d.n_total || k < 0 || k > b - a) bad = 1;
+        }
+        if (threadIdx.x == 0 && (off[0] != 0 || off[d.n_events] != c->n_active)) bad = 1;
+        if (__syncthreads_or(bad)) {
+            if (threadIdx.x == 0) atomicOr(&c->error, kErrOffsets);
+            return;
+        }
+    }
     long long carry_n = 0, carry_items = 0, carry_tiles = 0;
     unsigned long long pairs = 0, cs = 0;
     for (int base = 0; base < d.n_events; base += blockDim.x) {
@@ -385,6 +405,7 @@ __global__ void __launch_bounds__(kChunkThreads) small_tail_kernel(Dev d) {
     for (int p = p0; p < p1; ++p) {
         if (!d.keep8[p]) continue;
         const int id = src[p];
+        if (!GC_GUARD(q < d.n_total && id >= 0 && id < d.n_total)) continue;
         dst[q] = id;
         const int e = d.ev_of_id[id];
         const double ox = d.ev_origin[3 * e], oy = d.ev_origin[3 * e + 1], oz = d.ev_origin[3 * e + 2];
@@ -419,6 +440,7 @@ __global__ void loop_cond_kernel(Dev d, cudaGraphConditionalHandle h, int switch
 __global__ void __launch_bounds__(kChunkThreads) build_items_kernel(Dev d) {
     __shared__ long long s_warp[33];
     Ctrl *c = d.ctrl;
+    if (c->error) return;  // the offsets failed a check: they size nothing
     const int *off = d.ev_off[c->cur];
     long long carry = 0, carry_t = 0;
     for (int base = 0; base < d.n_events; base += kChunkThreads) {

@@ -19,14 +19,15 @@ from . import build as _build
 GC_ABI_VERSION = 2
 GC_OK, GC_INCOMPLETE = 0, 1
 GC_ERR_PARAM, GC_ERR_ALLOC, GC_ERR_CUDA, GC_ERR_STATE = -1, -2, -3, -4
-GC_ERR_DEVICE_TIMEOUT, GC_ERR_NO_DEVICE = -5, -6
+GC_ERR_DEVICE_TIMEOUT, GC_ERR_NO_DEVICE, GC_ERR_DEVICE_CHECK = -5, -6, -7
 GC_FP64, GC_FP32, GC_FP32_KAHAN, GC_FP16X2 = 0, 1, 2, 3
 
 # Every symbol include/gcoreccd.h declares.
 EXPORTS = ("gc_default_params", "gc_create", "gc_load_carriers", "gc_run", "gc_collect",
            "gc_image", "gc_positions", "gc_get_stats", "gc_coulomb_field",
            "gc_coulomb_field_noalloc", "gc_save_state", "gc_restore_state", "gc_destroy",
-           "gc_status_string", "gc_last_cuda_error", "gc_device_info", "gc_selftest_barrier_timeout")
+           "gc_status_string", "gc_last_cuda_error", "gc_device_info", "gc_selftest_barrier_timeout",
+           "gc_debug_inject")
 
 
 class GcParams(ctypes.Structure):
@@ -114,7 +115,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The release library, or with GCORECCD_DEBUG=1 in the environment the
+    GC_DEBUG build (bounds-checked kernels, fault planting)."""
+    return _build.LIB_DEBUG if os.environ.get("GCORECCD_DEBUG") == "1" else _build.LIB
 
 
 def load():
@@ -162,6 +165,8 @@ def load():
         L.gc_device_info.argtypes = [ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]
         L.gc_selftest_barrier_timeout.restype = I32
         L.gc_selftest_barrier_timeout.argtypes = [ctypes.c_double]
+        L.gc_debug_inject.restype = I32
+        L.gc_debug_inject.argtypes = [P, I32]
         _lib = L
         return L
 
@@ -200,6 +205,10 @@ def gc_default_params(**overrides) -> GcParams:
             raise AttributeError(f"gc_params has no field {k}")
         setattr(p, k, v)
     return p
+
+
+def gc_debug_inject(sim, what: int) -> None:
+    _check(load().gc_debug_inject(sim, int(what)), "gc_debug_inject")
 
 
 def gc_selftest_barrier_timeout(limit_s: float) -> int:
