@@ -212,21 +212,42 @@ def test_coulomb_off_diffusion_matches_oracle(gc):
     assert err < 1e-9
 
 
+# Per-carrier bounds of the reduced-precision forms on the 5.9 keV cloud
+# against the FP64 oracle (same diffusion stream, so only the rounding of
+# the field differs, and the Coulomb dynamics of the dense cloud amplify it
+# over ~1600 steps): for holes collected at the oracle's step, the median and
+# largest final |dxy| in um, and the least share of such holes.  Measured on
+# GB300: FP32 and FP32 + Kahan (identical here: one j-tile per chunk) 1.6e-3,
+# 0.40, 0.982; FP16x2 2.0e-2, 0.82, 0.874.
+XRAY_PER_CARRIER = {1: (5e-3, 1.0, 0.97), 2: (5e-3, 1.0, 0.97), 3: (5e-2, 2.0, 0.85)}
+
+
 @pytest.mark.parametrize("precision", [1, 2, 3])
 def test_fp32_xray_statistics(gc, precision):
     """FP32 pair sum on the 5.9 keV cloud: collected totals exact, sigma_x and
-    sigma_y within 0.5 %, image L1 difference <= 1 % of the charge."""
+    sigma_y within 0.5 %, image L1 difference <= 1 % of the charge, and the
+    per-carrier error against the FP64 oracle within the bounds above."""
     wl = I.xray_5p9kev()
     res = run_gpu(gc, wl, precision)
     ref = run_oracle(wl)
     assert res["status"] == 0
     assert res["n_collected"][0] == ref.n - ref.n_active()[0] == wl.n
     pos, rp = res["positions"], ref.positions()
+    sig = []
     for c in (0, 1):
+        sig.append(pos[:, c].std() / rp[:, c].std() - 1.0)
         assert pos[:, c].std() == pytest.approx(rp[:, c].std(), rel=5e-3)
     l1 = np.abs(res["image"].astype(np.int64) - ref.image.astype(np.int64)).sum()
     assert l1 <= 0.01 * wl.n
     assert int(res["image"].sum()) + int(res["n_offimage"][0]) == wl.n
+    same = res["collect_step"] == ref.collect_step
+    d = np.abs(pos[:, :2] - rp[:, :2]).max(axis=1)
+    med, mx, frac = XRAY_PER_CARRIER[precision]
+    print(f"5.9 keV cloud, precision {precision}: sigma_x err {sig[0]:+.2e}, sigma_y err {sig[1]:+.2e}, "
+          f"image L1 {l1}, same collection step {same.mean():.4f}, |dxy| of those: median "
+          f"{np.median(d[same]):.2e} um, max {d[same].max():.2e} um; all holes max {d.max():.2e} um")
+    assert same.mean() >= frac
+    assert np.median(d[same]) <= med and d[same].max() <= mx
 
 
 def test_graph_equals_eager_and_split_runs(gc):

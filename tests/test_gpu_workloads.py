@@ -137,7 +137,7 @@ def test_muon_field_forms_against_fp64(gc):
     # 1e-3 to 1e-2.  The FP16x2 form adds f16 rounding of r^2 (and f16
     # subnormals for the closest pairs at this event's scale).
     assert err32 < 5e-3
-    assert err16 < 2e-1
+    assert err16 < 1.2e-1  # measured 7.9e-2
 
 
 @pytest.fixture(scope="module")
@@ -175,3 +175,75 @@ def test_carriers_from_file_through_the_abi(gc, tmp_path):
     assert np.array_equal(res["collect_step"], ref.collect_step)
     assert np.array_equal(res["image"], ref.image)
     assert np.abs(res["positions"] - ref.positions()).max() < 1e-4
+
+
+def test_muon_50k_run_forms_against_fp64(gc):
+    """The muon geometry at a quarter of its density (50,000 holes of the
+    2.5 mm track): FP32 + Kahan and FP16x2 against the FP64 form on the GPU
+    over the first 150 steps (the FP64 form takes ~0.3 s per step here).
+    Same holes collected, same counts, per-hole |dr| within bounds."""
+    wl = I.subsample(I.muon_track(), 50_000, seed=9)
+    out = {}
+    for prec in (gc.GC_FP64, gc.GC_FP32_KAHAN, gc.GC_FP16X2):
+        p = gc.gc_default_params(precision=prec, img_w=wl.img_w, img_h=wl.img_h)
+        with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+            st, steps = sim.run(150)
+            assert steps == 150
+            r = sim.collect()
+            out[prec] = (sim.positions(), r["collect_step"], sim.image())
+    ref_pos, ref_cs, ref_img = out[gc.GC_FP64]
+    for prec, (mmax, frac) in ((gc.GC_FP32_KAHAN, (2e-2, 0.999)), (gc.GC_FP16X2, (1.0, 0.99))):
+        pos, cs, img = out[prec]
+        same = cs == ref_cs
+        d = np.linalg.norm(pos - ref_pos, axis=1)
+        n_col = int((cs >= 0).sum())
+        print(f"muon 50k, precision {prec}, 150 steps: {n_col} collected (FP64 {int((ref_cs >= 0).sum())}), "
+              f"same state {same.mean():.5f}, |dr|: median {np.median(d):.2e} um, 99th pct "
+              f"{np.percentile(d, 99):.2e} um, max {d.max():.2e} um")
+        assert same.mean() >= frac
+        assert abs(n_col - int((ref_cs >= 0).sum())) <= 0.01 * max(n_col, 1)
+        assert np.median(d) <= 1e-3 and d[same].max() <= mmax
+        assert np.abs(img.astype(np.int64) - ref_img.astype(np.int64)).sum() <= 0.01 * max(n_col, 1) + 2
+
+
+@pytest.fixture(scope="module")
+def full_batch(gc):
+    wl = I.xray_batch()
+    return wl, run(gc, wl, gc.GC_FP32_KAHAN)
+
+
+def test_full_batch_random_events_against_oracle(gc, full_batch):
+    """The whole 4096-event X-ray batch (1-18 keV) in one segmented run: counts
+    exact for every event, and 32 randomly chosen events against the FP64
+    oracle: sigma_x, sigma_y within 0.5 % for each; image L1 summed over the
+    32 events <= 1 % of their charge, and <= 2 % for each.  (Deep events live
+    ~5000 steps, over which the Coulomb dynamics amplify FP32 rounding: a few
+    tenths of a percent of their holes end one pixel over; worst measured
+    single-event L1 1.3 % of the charge.)"""
+    wl, res = full_batch
+    assert res["status"] == gc.GC_OK
+    sizes = np.diff(wl.ev_off)
+    assert np.array_equal(res["n_collected"], sizes)
+    rng = np.random.default_rng(2024)
+    worst_sig, worst_l1, l1_sum, charge = 0.0, 0.0, 0, 0
+    for e in rng.choice(wl.n_events, size=32, replace=False):
+        e = int(e)
+        ev = event_slice(wl, e)
+        ref = O.Simulation(O.make_params(img_w=wl.img_w, img_h=wl.img_h), ev.xyz, ev.ev_off, ev.seeds,
+                           ev.img_origin)
+        ref.run()
+        a, b = int(wl.ev_off[e]), int(wl.ev_off[e + 1])
+        assert np.all(ref.collect_step >= 0)
+        pos, rp = res["positions"][a:b], ref.positions()
+        for c in (0, 1):
+            err = pos[:, c].std() / rp[:, c].std() - 1.0
+            worst_sig = max(worst_sig, abs(err))
+            assert abs(err) <= 5e-3, (e, c, err)
+        l1 = int(np.abs(res["image"][e].astype(np.int64) - ref.image[0].astype(np.int64)).sum())
+        worst_l1 = max(worst_l1, l1 / (b - a))
+        assert l1 <= 0.02 * (b - a), (e, l1, b - a)
+        l1_sum += l1
+        charge += b - a
+    print(f"4096-event batch, 32 random events against the oracle: worst sigma error {worst_sig:.2e}, "
+          f"image L1 {l1_sum / charge:.2e} of the charge in all, worst event {worst_l1:.2e}")
+    assert l1_sum <= 0.01 * charge
