@@ -52,7 +52,10 @@ WORKLOADS = {
              "0.5 um jitter; " + FIELD + ", 512 x 512 pixels of 15 um"),
     "xray": ("xray-5.9keV: one cloud of 1573 holes, sigma 0.3 um, depth from seed 1; " + FIELD
              + ", 64 x 64 pixels of 15 um"),
+    "cloud-256": ("cloud-256: one cloud of 256 holes, sigma 0.5 um, at depth 300 um; " + FIELD
+                  + ", 32 x 32 pixels of 15 um"),
 }
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32k": 2, "fp16x2": 3}
 WORKLOAD = WORKLOADS["bundle"]
 
 
@@ -65,6 +68,8 @@ def make_workload(name: str):
         return inputs.muon_track()
     if name == "xray":
         return inputs.xray_5p9kev()
+    if name == "cloud-256":
+        return inputs.single_cloud()
     raise ValueError(name)
 
 
@@ -253,7 +258,7 @@ def to_completion(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     wl = make_workload(args.workload)
-    prec = gc.GC_FP32_KAHAN
+    prec = PRECISIONS[args.precision]
 
     def timed_run(w):
         p = gc.gc_default_params(precision=prec, img_w=w.img_w, img_h=w.img_h, pair_R=args.pair_R,
@@ -272,13 +277,15 @@ def to_completion(args):
     secs, steps, stats = timed_run(wl)
     line = {"metric": METRIC, "value": stats["pair_interactions"] / secs, "unit": "pairs/s",
             "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": 1e3 * secs / max(steps, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 0 else "f32", "precision": args.precision,
             "data": "synthetic", "mode": "to completion", "coulomb": args.coulomb,
             "stored_charge": args.stored_charge,
             "tile_frames": args.tile_frames,
             "config": {"workload": WORKLOADS[args.workload], "n_carriers": wl.n,
                        "events": wl.n_events, "pair_R": stats["pair_variant"],
-                       "jchunk": stats["jchunk"], "pair_blocks": stats["pair_blocks"]},
+                       "jchunk": stats["jchunk"], "pair_blocks": stats["pair_blocks"],
+                       "small_path": stats["fused_path"], "pair_kernel_variant": stats["pair_kernel_variant"]},
             "carrier_steps_per_s": stats["carrier_steps"] / secs, "seconds": secs,
             "pair_interactions": stats["pair_interactions"], "carrier_steps": stats["carrier_steps"]}
     if args.per_event and wl.n_events > 1:
@@ -418,6 +425,8 @@ def main():
                     help="with --to-completion: 1 adds the field of the charge stored in the pixels")
     ap.add_argument("--per-event", type=int, default=0,
                     help="with --to-completion: also run the first M events one simulation each")
+    ap.add_argument("--precision", default="fp32k", choices=sorted(PRECISIONS),
+                    help="with --to-completion: arithmetic of the pair sum")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if not args.coulomb:  # the O(N) path has its own metric; no end-to-end leg

@@ -145,9 +145,11 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
             const long long st = d.part_stride;
             if (!GC_GUARD(p >= 0 && p < d.n_total)) return false;
             const double *P = d.partial + p;
-            // loads of up to 8 chunks are issued before their (ordered) sums,
-            // so the chunk count does not chain memory round trips
-            constexpr int B = 8;
+            // fused kernels (few threads, latency-bound): the loads of up to 8
+            // chunks are issued before their (ordered) sums, so the chunk count
+            // does not chain memory round trips; the integrate kernel (1024
+            // threads, 64 registers) hides the latency with threads instead
+            constexpr int B = CG ? 8 : 1;
             for (int jc0 = 0; jc0 < js; jc0 += B) {
                 double v[B][3];
 #pragma unroll

@@ -302,30 +302,24 @@ __device__ __forceinline__ void finalize_block(const Dev &d, long long *s_warp) 
     const int cur = c->cur;
     const int *off = d.ev_off[cur];
     int *noff = d.ev_off[cur ^ 1];
-    // The active event offsets (and this step's collections) must be
-    // consistent before they size anything: otherwise flag kErrOffsets and
-    // leave the state alone; every later kernel then skips its step.
-    {
-        int bad = 0;
-        for (int e = threadIdx.x; e < d.n_events; e += blockDim.x) {
-            const int a = off[e], b = off[e + 1];
-            const int k = d.ev_collected_now[e];
-            if (a < 0 || b < a || b > d.n_total || k < 0 || k > b - a) bad = 1;
-        }
-        if (threadIdx.x == 0 && (off[0] != 0 || off[d.n_events] != c->n_active)) bad = 1;
-        if (__syncthreads_or(bad)) {
-            if (threadIdx.x == 0) atomicOr(&c->error, kErrOffsets);
-            return;
-        }
-    }
+    // The active event offsets (and this step's collections) are checked as
+    // they are read: an inconsistency sets kErrOffsets before anything they
+    // size is written (chunk counters, the control block); every later kernel
+    // then skips its step.  The prefixes written meanwhile (next buffers,
+    // one entry per event) are then never used.
+    int bad = 0;
+    if (threadIdx.x == 0 && (off[0] != 0 || off[d.n_events] != c->n_active)) bad = 1;
     long long carry_n = 0, carry_items = 0, carry_tiles = 0;
     unsigned long long pairs = 0, cs = 0;
     for (int base = 0; base < d.n_events; base += blockDim.x) {
         const int e = base + threadIdx.x;
         int n_old = 0, n_new = 0;
         if (e < d.n_events) {
-            n_old = off[e + 1] - off[e];
-            n_new = n_old - d.ev_collected_now[e];
+            const int a = off[e], b = off[e + 1];
+            const int k = d.ev_collected_now[e];
+            if (a < 0 || b < a || b > d.n_total || k < 0 || k > b - a) bad = 1;
+            n_old = b - a;
+            n_new = n_old - k;
             d.ev_collected_now[e] = 0;
         }
         pairs += (unsigned long long)n_old * (unsigned long long)n_old;
@@ -343,6 +337,10 @@ __device__ __forceinline__ void finalize_block(const Dev &d, long long *s_warp) 
         carry_n += tn;
         carry_items += ti;
         carry_tiles += tt;
+    }
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0) atomicOr(&c->error, kErrOffsets);
+        return;
     }
     // reduce the counters
     long long tot_pairs, tot_cs;
