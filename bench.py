@@ -103,8 +103,9 @@ def replica_seeds(seeds, rank: int):
 def recorded_traffic():
     """DRAM bytes per pair-kernel launch on the track-bundle workload, as
     recorded from one ncu capture in profiles/pair_fp32_track_bundle_traffic.txt
-    (key=value lines), only while the kernel source is the one that was
-    profiled (otherwise None): a recorded figure, not measured by this run."""
+    (key=value lines), only while the kernel source (gc_pair.cuh + pair.cu) is
+    the one that was profiled (otherwise None): a recorded figure, not
+    measured by this run."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "pair_fp32_track_bundle_traffic.txt")
     try:
@@ -114,10 +115,12 @@ def recorded_traffic():
             if "=" in line:
                 k, v = line.split("=", 1)
                 rec[k.strip()] = v.strip()
-        src = open(os.path.join(ROOT, "paper_2203_11043_gb300", "csrc", "pair.cu"), "rb").read()
+        h = hashlib.sha256()
+        for f in ("gc_pair.cuh", "pair.cu"):  # the pair kernel's templates and their instantiation
+            h.update(open(os.path.join(ROOT, "paper_2203_11043_gb300", "csrc", f), "rb").read())
     except OSError:
         return None
-    if rec.get("kernel_source_sha256") != hashlib.sha256(src).hexdigest():
+    if rec.get("kernel_source_sha256") != h.hexdigest():
         return None
     return float(rec["traffic_bytes_per_launch"])
 
@@ -486,11 +489,13 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
         for k in range(args.steps):
             flush.zero_()  # L2 flush between timed steps (256 MB > 129 MB L2)
             starts[k].record(stream)
             sim.run(1)
             ends[k].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
