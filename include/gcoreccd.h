@@ -101,11 +101,16 @@ typedef struct {
     int32_t fuse_small;    /* while at most 8192 holes are active: 0 = the four-launch step
                               throughout; 2 = each step two launches (a pair kernel that also
                               integrates every i-tile once its last j-chunk is summed, then one
-                              block that compacts); 1 (default) = as 2, except that one event
-                              (FP64, FP32 or FP32 + Kahan) runs all its remaining steps in one
-                              cooperative launch with one grid barrier per step.  All give the
-                              same results as the four-launch step.  Not used with newton, tile
-                              frames, stored charge or timing */
+                              block that compacts); 3 = as 2, except that one event (FP64, FP32,
+                              FP32 + Kahan) runs all its remaining steps in one cooperative
+                              launch with one grid barrier per step; 1 (default) = as 3, except
+                              that one FP32 / FP32 + Kahan event of at most 1280 active holes
+                              (and below the 4-lane threshold) runs all its steps in one
+                              thread-block cluster with its state in shared memory.  Paths 2 and
+                              3 give the same results as the four-launch step; the cluster sums
+                              each carrier's field in one piece with the lanes combined in FP32
+                              (the same FP32 error bound, not the same bits).  Not used with
+                              newton, tile frames, stored charge or timing */
     int32_t reserved0;
 } gc_params;
 
@@ -130,7 +135,8 @@ typedef struct {
     int32_t device_loop;          /* 1: gc_run is one graph launch with a device-side loop
                                      (conditional WHILE node over passes of graph_steps steps) */
     int32_t fused_path;           /* small-workload path of the last gc_run: 0 none, 1 two launches
-                                     per step, 2 the persistent single-event kernel */
+                                     per step, 2 the persistent single-event kernel, 3 the
+                                     cluster-resident single-event kernel */
     double tune_ms;               /* autotuner: host time spent choosing the pair-kernel shape at the
                                      last gc_load_carriers (0 when cached or off) */
     int32_t tune_candidates;      /* shapes timed at the last load */

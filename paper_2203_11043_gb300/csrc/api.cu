@@ -47,6 +47,12 @@ namespace {
         if (e_ != cudaSuccess) return cuda_fail(e_);   \
     } while (0)
 
+// Events of at most this many active holes take the cluster-resident kernel
+// (FP32 forms): measured per step, 256 holes 4.8 us there against 9.7-10.2 us
+// in the persistent kernel; at 1573 holes the cluster's 16 SMs are bound by
+// the pair arithmetic (15.8 us against 14.7 us).
+constexpr int kClusterPathMax = 1280;
+
 // Longest a device-side wait (a grid barrier of the persistent kernel) may
 // take before the kernel gives up with an error status.
 constexpr double kDeviceWaitLimitS = 1.0;
@@ -80,7 +86,7 @@ gc_status validate(const gc_params *p) {
     if ((p->coulomb | p->diffusion | p->reflect_back | p->autotune | p->newton | p->timing |
          p->stored_charge | p->tile_frames) & ~1)
         return GC_ERR_PARAM;
-    if (p->fuse_small < 0 || p->fuse_small > 2) return GC_ERR_PARAM;
+    if (p->fuse_small < 0 || p->fuse_small > 3) return GC_ERR_PARAM;
     if (p->pair_R != 0 && p->pair_R != 2 && p->pair_R != 4 && p->pair_R != 8) return GC_ERR_PARAM;
     return GC_OK;
 }
@@ -208,6 +214,7 @@ struct gc_sim {
     int fused_grid = 0;
     int fused_ran = 0;               // small-workload path of the last gc_run (gc_stats.fused_path)
     bool se_ok = false;              // the persistent single-event kernel applies
+    bool cluster_ok = false;         // the cluster-resident kernel may apply (FP32 forms, small event)
     int se_grid = 0;
     unsigned *h_probe = nullptr;     // pinned: items_total, work_counter of an autotuner probe
     int device_error = 0;            // Ctrl::error bits seen after the last load or run
@@ -250,6 +257,7 @@ void free_state(gc_sim *s) {
     s->fused_ok = false;
     s->fused_ran = 0;
     s->se_ok = false;
+    s->cluster_ok = false;
     for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
         for (cudaEvent_t e : *v) cudaEventDestroy(e);
         v->clear();
@@ -963,7 +971,9 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     // its shadows and keep bytes (keep bytes by slot, shadows by hole id)
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
-    s->se_ok = s->fused_ok && s->p.fuse_small == 1 && E == 1 && s->p.precision != GC_FP16X2 && coop;
+    s->se_ok = s->fused_ok && (s->p.fuse_small == 1 || s->p.fuse_small == 3) && E == 1 &&
+               s->p.precision != GC_FP16X2 && coop;
+    s->cluster_ok = s->se_ok && s->p.fuse_small == 1 && s->p.precision != GC_FP64;
     if (s->se_ok) {
         const size_t M = N;  // indexed by hole id
         for (int b = 0; b < 2; ++b) {
@@ -1092,6 +1102,22 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
         // are active, then (when available) the fused two-launch step.
         for (int phase = 0; phase < 2; ++phase) {
             const bool fz = s->fused_ok && s->h_ctrl->n_active <= kFusedMax;
+            const int na0 = s->h_ctrl->n_active;
+            if (fz && s->cluster_ok && na0 <= kClusterPathMax && na0 < s->dev.shape.small_n &&
+                cluster_path_available(s->p.precision, na0)) {
+                // one event below the 4-lane threshold: the whole remaining loop in one
+                // cluster, its state in shared memory
+                s->fused_ran = 3;
+                GC_CUDA(launch_cluster_event(s->dev, s->p.precision, na0, s->stream));
+                r = read_ctrl(s);
+                if (r != GC_OK) return r;
+                if (s->h_ctrl->error) {
+                    s->device_error = s->h_ctrl->error;
+                    return device_error_status(s->device_error);
+                }
+                GC_CUDA(launch_build_items(s->dev, s->stream));  // items in the other paths' layout
+                break;
+            }
             if (fz && s->se_ok) {
                 // one event, few holes: the whole remaining loop in one cooperative launch
                 s->fused_ran = 2;

@@ -64,6 +64,13 @@ cudaError_t launch_small_tail(const Dev &d, bool fp64, cudaStream_t st);
 const void *se_kernel_ptr(int precision, int R);
 int se_occupancy(int precision, int R);
 cudaError_t launch_se_loop(const Dev &d, int precision, int grid, double limit_s, cudaStream_t st);
+// Cluster-resident single-event kernel (one event below the 4-lane threshold,
+// at most 2048 active holes, FP32 or FP32 + Kahan): every step until
+// completion or the step limit in one launch of one cluster of
+// cluster_ctas_for(n) CTAs; availability checks that such a cluster fits.
+int cluster_ctas_for(int n);
+bool cluster_path_available(int precision, int n);
+cudaError_t launch_cluster_event(const Dev &d, int precision, int n, cudaStream_t st);
 // Runs a barrier that can never complete on `grid` co-resident blocks; the
 // error bits it leaves (kErrBarrierTimeout expected) go to *error_bits.
 cudaError_t selftest_barrier_timeout(int grid, double limit_s, int *error_bits, cudaStream_t st);

@@ -128,10 +128,13 @@ __device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, 
 // from other SMs, so this SM's L1 may hold a stale copy of their lines.
 // advance_hole: hole `id` of event e (n_e active holes; read only with the
 // Coulomb field on) at (x, y, z), whose per-chunk partial sums sit at slot p;
-// on return (x, y, z) is the new position (also stored).
-template <bool F64, bool INIT, bool CG = false>
+// on return (x, y, z) is the new position (also stored).  GIVEN: the caller
+// passes (gx, gy, gz), the sums of the per-chunk partials accumulated from 0.0
+// in chunk order (the same bits as the loop below), instead of slot p.
+template <bool F64, bool INIT, bool CG = false, bool GIVEN = false>
 __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_e, int p, long long step,
-                                             double &x, double &y, double &z) {
+                                             double &x, double &y, double &z, double gx = 0.0,
+                                             double gy = 0.0, double gz = 0.0) {
     const Phys &ph = d.phys;
     if (INIT) {
         if (ph.reflect && z > ph.thickness) {
@@ -140,7 +143,11 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
         }
     } else {
         double ex = 0.0, ey = 0.0, ez = 0.0;
-        if (ph.coulomb) {  // Eq. 6: sum of the per-chunk partial sums, fixed order
+        if (ph.coulomb && GIVEN) {
+            ex = gx;
+            ey = gy;
+            ez = gz;
+        } else if (ph.coulomb) {  // Eq. 6: sum of the per-chunk partial sums, fixed order
             const int js = ceil_div(n_e, d.shape.jchunk);
             const long long st = d.part_stride;
             if (!GC_GUARD(p >= 0 && p < d.n_total)) return false;
@@ -176,6 +183,8 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                     }
                 }
             }
+        }
+        if (ph.coulomb) {
             ex *= ph.K;
             ey *= ph.K;
             ez *= ph.K;

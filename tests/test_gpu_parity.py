@@ -542,29 +542,33 @@ def test_small_paths_equal_four_launch_step(gc, precision):
     batch, with graphs and eagerly."""
     for wl, kw, single in ((I.xray_5p9kev(), {}, True), (ragged_batch(), dict(pixel_um=1.0), False)):
         se = 2 if (single and precision != 3) else 1
+        cases = [(0, 32, 0), (2, 32, 1), (2, 0, 1), (3, 32, se), (3, 0, se)]
+        if not single:  # a batch takes the two-launch path by default
+            cases += [(1, 32, 1), (1, 0, 1)]
         outs = []
-        for fuse, gs, path in ((0, 32, 0), (2, 32, 1), (2, 0, 1), (1, 32, se), (1, 0, se)):
-            res = run_gpu(gc, wl, precision, fuse_small=fuse, graph_steps=gs, **kw)
+        for fuse, gs, path in cases:
+            res = run_gpu(gc, wl, precision, fuse_small=fuse, graph_steps=gs, autotune=0, **kw)
             assert res["stats"]["fused_path"] == path, (fuse, gs)
             outs.append(res)
         for o in outs[1:]:
             assert_same_run(o, outs[0])
 
 
-@pytest.mark.parametrize("precision", [0, 2])
-def test_persistent_kernel_split_runs(gc, precision):
-    """The persistent kernel stops at the step limit of each gc_run and writes
-    the state back; runs split into pieces give the bits of one run."""
+@pytest.mark.parametrize("precision,fuse,path", [(0, 1, 2), (2, 3, 2), (2, 1, 3), (1, 1, 3)])
+def test_persistent_kernel_split_runs(gc, precision, fuse, path):
+    """The persistent kernel (path 2) and the cluster kernel (path 3) stop at
+    the step limit of each gc_run and write the state back; runs split into
+    pieces give the bits of one run."""
     wl = I.single_cloud(n=700, sigma_um=0.4, z0_um=30.0, seed=19, img=32)
     outs = []
     for pieces in ([-1], [1, 7, 50, -1]):
-        p = gc.gc_default_params(precision=precision, img_w=32, img_h=32)
+        p = gc.gc_default_params(precision=precision, img_w=32, img_h=32, fuse_small=fuse, autotune=0)
         with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
             done = 0
             for k in pieces:
                 done += sim.run(k)[1]
             st = sim.stats()
-            assert st["fused_path"] == 2 and st["n_active"] == 0
+            assert st["fused_path"] == path and st["n_active"] == 0
             outs.append((done, sim.positions(), sim.collect()["collect_step"], sim.image(),
                          st["pair_interactions"], st["carrier_steps"]))
     assert outs[0][0] == outs[1][0]
@@ -593,7 +597,7 @@ def test_fused_takes_over_below_its_limit(gc):
     the same bits as a run on the four-launch step throughout."""
     wl = I.single_cloud(n=12000, sigma_um=0.6, z0_um=20.0, seed=44, img=32)
     a = run_gpu(gc, wl, 2, fuse_small=0)
-    for fuse, path in ((2, 1), (1, 2)):
+    for fuse, path in ((2, 1), (3, 2)):
         b = run_gpu(gc, wl, 2, fuse_small=fuse)
         assert a["stats"]["fused_path"] == 0 and b["stats"]["fused_path"] == path
         assert_same_run(a, b)
@@ -640,3 +644,33 @@ def test_pair_shape_knobs_do_not_change_results(gc):
             sim.run(3)
             outs.append(sim.positions())
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_cluster_path_against_oracle_and_deterministic(gc, precision):
+    """One FP32 event of at most 1280 holes runs every step inside one
+    thread-block cluster (path 3), summing the field over the whole j range
+    and combining lanes in FP32: not the other paths' bits, but the same
+    acceptance against the FP64 oracle (totals exact, sigma within 0.5 %,
+    image L1 <= 1 %, per-carrier bounds of the FP32 forms), the same result
+    with and without graphs, and from run to run."""
+    wl = I.single_cloud(n=1000, sigma_um=0.3, z0_um=250.0, seed=71, img=64)
+    ref = run_oracle(wl)
+    outs = [run_gpu(gc, wl, precision, graph_steps=gs, autotune=0) for gs in (32, 0, 32)]
+    for o in outs:
+        assert o["stats"]["fused_path"] == 3 and o["status"] == 0
+    for o in outs[1:]:
+        assert_same_run(o, outs[0])
+    res = outs[0]
+    assert res["n_collected"][0] == wl.n
+    pos, rp = res["positions"], ref.positions()
+    for c in (0, 1):
+        assert pos[:, c].std() == pytest.approx(rp[:, c].std(), rel=5e-3)
+    l1 = np.abs(res["image"].astype(np.int64) - ref.image.astype(np.int64)).sum()
+    assert l1 <= 0.01 * wl.n
+    same = res["collect_step"] == ref.collect_step
+    d = np.abs(pos[:, :2] - rp[:, :2]).max(axis=1)
+    med, mx, frac = XRAY_PER_CARRIER[precision]
+    print(f"cluster path, precision {precision}: image L1 {l1}, same collection step {same.mean():.4f}, "
+          f"|dxy| median {np.median(d[same]):.2e} um, max {d[same].max():.2e} um")
+    assert same.mean() >= frac and np.median(d[same]) <= med and d[same].max() <= mx

@@ -102,12 +102,14 @@ def test_batch_events_against_oracle(gc, batch):
 def test_batched_equals_per_event(gc, batch):
     """An event inside the batch is bit-identical to the same event alone
     (with the pair shape pinned: the autotuner may choose a different 4-lane
-    threshold or j-chunk for a different workload)."""
+    threshold or j-chunk for a different workload; and on the paths that
+    share the items and partial sums: not the cluster path, which sums each
+    small event in one piece)."""
     wl, res = batch
     sizes = np.diff(wl.ev_off)
     for e in [int(np.argmin(sizes)), 7, int(np.argmax(sizes))]:
         ev = event_slice(wl, e)
-        alone = run(gc, ev, gc.GC_FP32_KAHAN, pair_R=4, jchunk=8192, autotune=0)
+        alone = run(gc, ev, gc.GC_FP32_KAHAN, pair_R=4, jchunk=8192, autotune=0, fuse_small=3)
         a, b = int(wl.ev_off[e]), int(wl.ev_off[e + 1])
         assert np.array_equal(alone["positions"], res["positions"][a:b])
         assert np.array_equal(alone["collect_step"], res["collect_step"][a:b])
