@@ -266,7 +266,7 @@ def to_completion(args):
     def timed_run(w):
         p = gc.gc_default_params(precision=prec, img_w=w.img_w, img_h=w.img_h, pair_R=args.pair_R,
                                  coulomb=args.coulomb, stored_charge=args.stored_charge,
-                                 tile_frames=args.tile_frames)
+                                 tile_frames=args.tile_frames, fuse_small=args.fuse_small)
         with gc.Simulation(p, w.xyz, w.ev_off, w.seeds, w.img_origin, stream=stream.cuda_stream) as s:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -428,6 +428,8 @@ def main():
                     help="with --to-completion: 1 adds the field of the charge stored in the pixels")
     ap.add_argument("--per-event", type=int, default=0,
                     help="with --to-completion: also run the first M events one simulation each")
+    ap.add_argument("--fuse-small", type=int, default=1, choices=[0, 1, 2, 3, 4],
+                    help="small-workload path (gc_params.fuse_small; 1 = automatic)")
     ap.add_argument("--precision", default="fp32k", choices=sorted(PRECISIONS),
                     help="with --to-completion: arithmetic of the pair sum")
     args = ap.parse_args()

@@ -103,14 +103,22 @@ typedef struct {
                               integrates every i-tile once its last j-chunk is summed, then one
                               block that compacts); 3 = as 2, except that one event (FP64, FP32,
                               FP32 + Kahan) runs all its remaining steps in one cooperative
-                              launch with one grid barrier per step; 1 (default) = as 3, except
-                              that one FP32 / FP32 + Kahan event of at most 1280 active holes
-                              (and below the 4-lane threshold) runs all its steps in one
-                              thread-block cluster with its state in shared memory.  Paths 2 and
-                              3 give the same results as the four-launch step; the cluster sums
-                              each carrier's field in one piece with the lanes combined in FP32
-                              (the same FP32 error bound, not the same bits).  Not used with
-                              newton, tile frames, stored charge or timing */
+                              launch with one grid barrier per step (the persistent kernel);
+                              4 = as 2, except that one FP32 / FP32 + Kahan event of at most
+                              4096 active holes runs all its steps in one cooperative launch of
+                              one CTA per SM, each CTA owning a fixed set of holes and the CTAs
+                              exchanging step-tagged shadow words instead of passing a barrier
+                              (the grid-resident kernel); 5 = as 2, except that one FP32 /
+                              FP32 + Kahan event of at most 2048 active holes runs all its steps
+                              in one thread-block cluster with its state in shared memory;
+                              1 (default) = one FP32 / FP32 + Kahan event takes the persistent
+                              kernel while more than 4096 holes are active and the grid-resident
+                              kernel from there, one FP64 event the persistent kernel, a batch
+                              the path of 2.  Paths 2 and 3 give the same results as the
+                              four-launch step; the grid-resident and cluster kernels sum each
+                              carrier's field in one piece with the lanes combined in FP32 (the
+                              same FP32 error bound, not the same bits).  Not used with newton,
+                              tile frames, stored charge or timing */
     int32_t reserved0;
 } gc_params;
 
@@ -136,7 +144,8 @@ typedef struct {
                                      (conditional WHILE node over passes of graph_steps steps) */
     int32_t fused_path;           /* small-workload path of the last gc_run: 0 none, 1 two launches
                                      per step, 2 the persistent single-event kernel, 3 the
-                                     cluster-resident single-event kernel */
+                                     cluster-resident single-event kernel, 4 the grid-resident
+                                     single-event kernel */
     double tune_ms;               /* autotuner: host time spent choosing the pair-kernel shape at the
                                      last gc_load_carriers (0 when cached or off) */
     int32_t tune_candidates;      /* shapes timed at the last load */

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libgcoreccd.so")
 LIB_DEBUG = os.path.join(OUT_DIR, "libgcoreccd_debug.so")  # GC_DEBUG: bounds-checked kernels
-SOURCES = ["pair.cu", "fused.cu", "se.cu", "cluster.cu", "step.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["pair.cu", "fused.cu", "se.cu", "cluster.cu", "resident.cu", "step.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

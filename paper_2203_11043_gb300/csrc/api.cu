@@ -47,11 +47,12 @@ namespace {
         if (e_ != cudaSuccess) return cuda_fail(e_);   \
     } while (0)
 
-// Events of at most this many active holes take the cluster-resident kernel
-// (FP32 forms): measured per step, 256 holes 4.8 us there against 9.7-10.2 us
-// in the persistent kernel; at 1573 holes the cluster's 16 SMs are bound by
-// the pair arithmetic (15.8 us against 14.7 us).
-constexpr int kClusterPathMax = 1280;
+// One FP32 / FP32 + Kahan event of at most this many active holes takes the
+// grid-resident kernel by default.  Measured per step to completion (clouds at
+// 300 um, FP32 + Kahan): 256 holes 4.2 us there, 4.7 us in the cluster kernel,
+// 10.3 us in the persistent kernel; 1573 holes 6.2, -, 14.7 us; 4096 holes
+// 15.1 us against 28.1 us in the persistent kernel.
+constexpr int kResidentPathMax = 4096;
 
 // Longest a device-side wait (a grid barrier of the persistent kernel) may
 // take before the kernel gives up with an error status.
@@ -86,7 +87,7 @@ gc_status validate(const gc_params *p) {
     if ((p->coulomb | p->diffusion | p->reflect_back | p->autotune | p->newton | p->timing |
          p->stored_charge | p->tile_frames) & ~1)
         return GC_ERR_PARAM;
-    if (p->fuse_small < 0 || p->fuse_small > 3) return GC_ERR_PARAM;
+    if (p->fuse_small < 0 || p->fuse_small > 5) return GC_ERR_PARAM;
     if (p->pair_R != 0 && p->pair_R != 2 && p->pair_R != 4 && p->pair_R != 8) return GC_ERR_PARAM;
     return GC_OK;
 }
@@ -205,7 +206,7 @@ struct gc_sim {
     DevAllocs mem;
     Dev dev{};
     Ctrl *h_ctrl = nullptr;          // pinned mirror of the device control block
-    long long *h_limit = nullptr;    // pinned staging for step_limit and loop_last
+    long long *h_limit = nullptr;    // pinned staging for step_limit, loop_last and stop_below
     cudaGraphExec_t graph = nullptr;
     bool graph_loops = false;        // the graph holds a device-side WHILE loop over K-step passes
     // fused small-workload path: two launches per step while at most kFusedMax
@@ -215,6 +216,7 @@ struct gc_sim {
     int fused_ran = 0;               // small-workload path of the last gc_run (gc_stats.fused_path)
     bool se_ok = false;              // the persistent single-event kernel applies
     bool cluster_ok = false;         // the cluster-resident kernel may apply (FP32 forms, small event)
+    bool resident_ok = false;        // the grid-resident kernel may apply (FP32 forms, one event)
     int se_grid = 0;
     unsigned *h_probe = nullptr;     // pinned: items_total, work_counter of an autotuner probe
     int device_error = 0;            // Ctrl::error bits seen after the last load or run
@@ -258,6 +260,7 @@ void free_state(gc_sim *s) {
     s->fused_ran = 0;
     s->se_ok = false;
     s->cluster_ok = false;
+    s->resident_ok = false;
     for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
         for (cudaEvent_t e : *v) cudaEventDestroy(e);
         v->clear();
@@ -301,7 +304,8 @@ gc_status read_ctrl(gc_sim *s) {
 gc_status set_limit(gc_sim *s, long long limit) {
     s->h_limit[0] = limit;
     s->h_limit[1] = -1;  // loop_last: the next device-side loop starts afresh
-    GC_CUDA(cudaMemcpyAsync(&s->dev.ctrl->step_limit, s->h_limit, 2 * sizeof(long long),
+    s->h_limit[2] = s->resident_ok ? kResidentPathMax : 0;  // the other paths hand over to it there
+    GC_CUDA(cudaMemcpyAsync(&s->dev.ctrl->step_limit, s->h_limit, 3 * sizeof(long long),
                             cudaMemcpyHostToDevice, s->stream));
     GC_CUDA(cudaStreamSynchronize(s->stream));
     return GC_OK;
@@ -795,7 +799,7 @@ gc_status gc_create(const gc_params *p, void *cuda_stream, gc_sim **out) {
             s->own_stream = true;
         }
         if ((e = cudaMallocHost((void **)&s->h_ctrl, sizeof(Ctrl))) != cudaSuccess) { st = cuda_fail(e); break; }
-        if ((e = cudaMallocHost((void **)&s->h_limit, 2 * sizeof(long long))) != cudaSuccess) { st = cuda_fail(e); break; }
+        if ((e = cudaMallocHost((void **)&s->h_limit, 3 * sizeof(long long))) != cudaSuccess) { st = cuda_fail(e); break; }
         if ((e = cudaMallocHost((void **)&s->h_probe, 2 * sizeof(unsigned))) != cudaSuccess) { st = cuda_fail(e); break; }
         std::memset(s->h_ctrl, 0, sizeof(Ctrl));
     } while (0);
@@ -973,7 +977,13 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
     s->se_ok = s->fused_ok && (s->p.fuse_small == 1 || s->p.fuse_small == 3) && E == 1 &&
                s->p.precision != GC_FP16X2 && coop;
-    s->cluster_ok = s->se_ok && s->p.fuse_small == 1 && s->p.precision != GC_FP64;
+    const bool fp32 = s->p.precision == GC_FP32 || s->p.precision == GC_FP32_KAHAN;
+    s->cluster_ok = s->fused_ok && s->p.fuse_small == 5 && E == 1 && fp32;
+    s->resident_ok = s->fused_ok && (s->p.fuse_small == 1 || s->p.fuse_small == 4) && E == 1 && fp32 && coop &&
+                     resident_path_available(s->p.precision, kResidentPathMax, s->sm_count);
+    if (s->resident_ok) {
+        GC_ALLOC(d.rs_rec, resident_words_bytes())
+    }
     if (s->se_ok) {
         const size_t M = N;  // indexed by hole id
         for (int b = 0; b < 2; ++b) {
@@ -1067,7 +1077,7 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     r = read_ctrl(s);
     if (r != GC_OK) return r;
     s->launches_per_step = (s->fused_ok && s->h_ctrl->n_active <= kFusedMax)
-                               ? (s->se_ok ? 0 : 2)
+                               ? ((s->se_ok || s->resident_ok || s->cluster_ok) ? 0 : 2)
                                : (s->phys.coulomb ? 1 : 0) + (s->phys.stored ? 1 : 0) + (frames ? 1 : 0) + 3;
     if (s->p.timing) {
         for (auto *v : {&s->ev_a, &s->ev_b, &s->ev_c, &s->ev_d}) {
@@ -1098,14 +1108,32 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
         if (r != GC_OK) return r;
         const int K = use_graph(s) ? s->p.graph_steps : 1;
         s->fused_ran = false;
-        // Up to two phases: the unfused step while more than kFusedMax holes
-        // are active, then (when available) the fused two-launch step.
-        for (int phase = 0; phase < 2; ++phase) {
+        // Up to three phases: the unfused step while more than kFusedMax holes
+        // are active, then (when available) a small-workload path: the
+        // persistent kernel until at most kResidentPathMax holes are active
+        // and the grid-resident kernel from there (one FP32 event), or one of
+        // the others.
+        for (int phase = 0; phase < 3; ++phase) {
             const bool fz = s->fused_ok && s->h_ctrl->n_active <= kFusedMax;
             const int na0 = s->h_ctrl->n_active;
-            if (fz && s->cluster_ok && na0 <= kClusterPathMax && na0 < s->dev.shape.small_n &&
-                cluster_path_available(s->p.precision, na0)) {
-                // one event below the 4-lane threshold: the whole remaining loop in one
+            if (fz && s->resident_ok && na0 <= kResidentPathMax &&
+                resident_path_available(s->p.precision, na0, s->sm_count)) {
+                // one event: the whole remaining loop on every SM, each CTA owning
+                // a fixed set of holes, no grid barrier between steps
+                s->fused_ran = 4;
+                GC_CUDA(launch_resident_event(s->dev, s->p.precision, na0, s->sm_count, kDeviceWaitLimitS,
+                                              s->stream));
+                r = read_ctrl(s);
+                if (r != GC_OK) return r;
+                if (s->h_ctrl->error) {
+                    s->device_error = s->h_ctrl->error;
+                    return device_error_status(s->device_error);
+                }
+                GC_CUDA(launch_build_items(s->dev, s->stream));  // items in the other paths' layout
+                break;
+            }
+            if (fz && s->cluster_ok && cluster_path_available(s->p.precision, na0)) {
+                // one event of at most 2048 holes: the whole remaining loop in one
                 // cluster, its state in shared memory
                 s->fused_ran = 3;
                 GC_CUDA(launch_cluster_event(s->dev, s->p.precision, na0, s->stream));
@@ -1135,6 +1163,7 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
                     return device_error_status(s->device_error);
                 }
                 GC_CUDA(launch_build_items(s->dev, s->stream));  // items in the other paths' layout
+                if (s->resident_ok && s->h_ctrl->n_active > 0 && s->h_ctrl->step < limit) continue;
                 break;
             }
             if (fz) s->fused_ran = 1;
@@ -1197,12 +1226,17 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
                     r = read_ctrl(s);
                     if (r != GC_OK) return r;
                     if (s->h_ctrl->n_active <= 0 || s->h_ctrl->step >= limit) break;
-                    if (s->h_ctrl->step == before) return GC_ERR_STATE;  // no progress: never spin
                     if (!fz && s->fused_ok && s->h_ctrl->n_active <= kFusedMax) break;  // hand over
+                    if (s->resident_ok && s->h_ctrl->n_active <= kResidentPathMax) break;  // hand over
+                    if (s->h_ctrl->step == before) return GC_ERR_STATE;  // no progress: never spin
                 }
             }
-            if (fz || s->h_ctrl->n_active <= 0 || s->h_ctrl->step >= limit) break;
-            if (!(s->fused_ok && s->h_ctrl->n_active <= kFusedMax)) break;
+            if (s->h_ctrl->n_active <= 0 || s->h_ctrl->step >= limit) break;
+            // the next phase: a small-workload path below kFusedMax, the grid-resident
+            // kernel below kResidentPathMax
+            if (fz ? !(s->resident_ok && s->h_ctrl->n_active <= kResidentPathMax)
+                   : !(s->fused_ok && s->h_ctrl->n_active <= kFusedMax))
+                break;
         }
         if (s->h_ctrl->error) {
             s->device_error = s->h_ctrl->error;

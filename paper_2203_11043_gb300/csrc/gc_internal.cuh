@@ -44,6 +44,8 @@ struct Ctrl {
     long long step;          // time steps completed
     long long step_limit;    // stop when step reaches this (set by the host)
     long long loop_last;     // step seen by the previous pass of a device-side loop
+    long long stop_below;    // steps pause once at most this many carriers are active (set by
+                             // the host: the hand-over to the grid-resident kernel; 0 = never)
     int n_active;            // active carriers at the start of the next step
     int cur;                 // which of the double-buffered active lists is current
     int items_total;         // pair work items for the next step
@@ -127,6 +129,9 @@ struct Dev {
     float4 *se_sh32[2];
     double4_32a *se_sh64[2];
     unsigned char *se_keep[2];
+    // grid-resident single-event kernel: each hole's published words (FP32
+    // shadow coordinate + step tag + keep bit), [parity][coordinate][slot at launch]
+    unsigned long long *rs_rec;
     Ctrl *ctrl;
     int n_total;
     int n_events;
@@ -153,10 +158,14 @@ constexpr int kErrOffsets = 2;         // the active event offsets are inconsist
 constexpr int kErrIndex = 4;           // a GC_DEBUG bounds check failed (the access was skipped)
 
 // A step is skipped when the run limit is reached, nothing is active, or a
-// device-side check has failed (no kernel then uses the state again).
-__device__ inline bool step_skipped(const Ctrl *c) {
+// device-side check has failed (no kernel then uses the state again); the
+// steps of every path but the grid-resident kernel also pause once at most
+// stop_below carriers are active, so that it takes over at a step fixed by
+// the state alone.
+__device__ inline bool run_over(const Ctrl *c) {
     return c->step >= c->step_limit || c->n_active <= 0 || c->error != 0;
 }
+__device__ inline bool step_skipped(const Ctrl *c) { return run_over(c) || c->n_active <= c->stop_below; }
 
 // GC_DEBUG builds check the index behind each data-dependent access: a failed
 // check sets kErrIndex and the access is skipped (never a trap).  Release

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "gcoreccd.h"
@@ -60,17 +61,29 @@ cudaError_t launch_small_tail(const Dev &d, bool fp64, cudaStream_t st);
 // FP64 form or FP32 forms without FP16x2, Newton step, tile frames or stored
 // charge): every step until completion or the step limit in one cooperative
 // launch of `grid` blocks (at most se_occupancy(...) per SM), one grid barrier
-// per step whose waits give up after limit_s (kErrBarrierTimeout).
+// per step whose waits give up after limit_s (kErrBarrierTimeout); like every
+// step it pauses once at most Ctrl::stop_below holes are active.
 const void *se_kernel_ptr(int precision, int R);
 int se_occupancy(int precision, int R);
 cudaError_t launch_se_loop(const Dev &d, int precision, int grid, double limit_s, cudaStream_t st);
-// Cluster-resident single-event kernel (one event below the 4-lane threshold,
-// at most 2048 active holes, FP32 or FP32 + Kahan): every step until
-// completion or the step limit in one launch of one cluster of
-// cluster_ctas_for(n) CTAs; availability checks that such a cluster fits.
+// Cluster-resident single-event kernel (one event of at most 2048 active
+// holes, FP32 or FP32 + Kahan): every step until completion or the step limit
+// in one launch of one cluster of cluster_ctas_for(n) CTAs; availability
+// checks that such a cluster fits.
 int cluster_ctas_for(int n);
 bool cluster_path_available(int precision, int n);
 cudaError_t launch_cluster_event(const Dev &d, int precision, int n, cudaStream_t st);
+// Grid-resident single-event kernel (one event of at most 4096 active holes,
+// FP32 or FP32 + Kahan): every step until completion or the step limit in one
+// cooperative launch of resident_grid(sm_count, n) CTAs, each owning a fixed
+// set of holes, exchanging step-tagged words instead of a grid barrier; its
+// waits give up after limit_s (kErrBarrierTimeout).  The words take
+// resident_words_bytes() of device memory (Dev::rs_rec).
+size_t resident_words_bytes();
+int resident_grid(int sm_count, int n);
+bool resident_path_available(int precision, int n, int sm_count);
+cudaError_t launch_resident_event(const Dev &d, int precision, int n, int sm_count, double limit_s,
+                                  cudaStream_t st);
 // Runs a barrier that can never complete on `grid` co-resident blocks; the
 // error bits it leaves (kErrBarrierTimeout expected) go to *error_bits.
 cudaError_t selftest_barrier_timeout(int grid, double limit_s, int *error_bits, cudaStream_t st);

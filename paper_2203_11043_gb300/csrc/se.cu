@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kPairThreads, F64 ? 5 : 1) se_loop_kernel(Dev 
     using Shadow = typename std::conditional<F64, double4_32a, float4>::type;
     Ctrl *c = d.ctrl;
     if (step_skipped(c)) return;  // uniform: nothing changes the control block before the first barrier
-    const long long limit = c->step_limit;
+    const long long limit = c->step_limit, stop_below = c->stop_below;
     long long step = c->step;
     const int cur = c->cur;
     const int *act0 = d.act[cur];
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kPairThreads, F64 ? 5 : 1) se_loop_kernel(Dev 
         csteps += (unsigned long long)n;
         n = se_compact_list(s_list, keep, n, s_warp);
         ++step;
-        if (n == 0 || step >= limit) break;
+        if (n <= stop_below || n == 0 || step >= limit) break;  // (stop_below: a hand-over)
     }
     if (blockIdx.x != 0) return;
     // block 0: the state in the layout of the other paths (active list and
@@ -221,7 +221,6 @@ __global__ void __launch_bounds__(kPairThreads, F64 ? 5 : 1) se_loop_kernel(Dev 
 }
 
 // ---- launch ------------------------------------------------------------------
-typedef void (*SEKernel)(Dev, unsigned long long);
 
 const void *se_kernel_ptr(int precision, int R) {
     if (precision == 0) return (const void *)se_loop_kernel<1, false, true>;

@@ -428,8 +428,8 @@ __global__ void __launch_bounds__(kChunkThreads) small_tail_kernel(Dev d) {
 __global__ void loop_cond_kernel(Dev d, cudaGraphConditionalHandle h, int switch_below) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     Ctrl *c = d.ctrl;
-    const bool go = c->n_active > switch_below && c->n_active > 0 && c->step < c->step_limit &&
-                    c->step != c->loop_last;
+    const bool go = c->n_active > switch_below && c->n_active > c->stop_below && c->n_active > 0 &&
+                    c->step < c->step_limit && c->step != c->loop_last;
     c->loop_last = c->step;
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }

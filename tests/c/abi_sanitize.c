@@ -19,7 +19,7 @@ int main(void) {
     bad.dt_s = -1.0;
     EXPECT(gc_create(&bad, NULL, &s) == GC_ERR_PARAM && s == NULL);
     bad = p;
-    bad.fuse_small = 3;
+    bad.fuse_small = 6;
     EXPECT(gc_create(&bad, NULL, &s) == GC_ERR_PARAM);
     bad = p;
     bad.img_w = 0;

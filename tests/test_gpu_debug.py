@@ -1,8 +1,8 @@
 """The GC_DEBUG build (bounds-checked kernels) and the device-side checks.
 
   * On valid inputs the checks stay silent: every path (four-launch step,
-    two-launch fused step, persistent single-event kernel, FP64 form) runs
-    with the error word 0 and gives the release build's bits (the checks
+    two-launch fused step, the persistent, cluster-resident and
+    grid-resident single-event kernels, FP64 form) runs with the error word 0 and gives the release build's bits (the checks
     only guard accesses; the arithmetic is the same).
   * A planted fault -- event offsets that do not match the carriers, written
     on the host before upload (gc_debug_inject) -- is caught on the device
@@ -64,15 +64,16 @@ print(json.dumps(out))
 
 
 def cases():
-    """(name, workload, parameters) run in both builds: the cluster kernel and
-    the persistent kernel (one small event), the two-launch fused step (a
-    batch), the four-launch step throughout and with the hand-over (a larger
-    event), and the FP64 form."""
+    """(name, workload, parameters) run in both builds: the cluster kernel,
+    the persistent kernel and the grid-resident kernel (one small event), the
+    two-launch fused step (a batch), the four-launch step throughout and with
+    the hand-over (a larger event), and the FP64 form."""
     big = I.single_cloud(n=12000, sigma_um=0.6, z0_um=20.0, seed=44, img=32)
     batch = I.xray_batch(n_events=24)
     # the j-chunk is pinned: occupancy (and so the automatic j-chunk) differs between the builds
-    return [("cluster_fp32", I.xray_5p9kev(), dict(precision=2, jchunk=512)),
+    return [("cluster_fp32", I.xray_5p9kev(), dict(precision=2, jchunk=512, fuse_small=5)),
             ("se_fp32", I.xray_5p9kev(), dict(precision=2, jchunk=512, fuse_small=3)),
+            ("resident_fp32", I.xray_5p9kev(), dict(precision=2, fuse_small=4)),
             ("fused_batch", batch, dict(precision=2, jchunk=2048)),
             ("four_launch", big, dict(precision=2, fuse_small=0, jchunk=2048)),
             ("handover", big, dict(precision=2, jchunk=2048)),

@@ -367,12 +367,12 @@ def test_large_one_step_sampled(gc):
 
 
 def test_timing_mode_counts_pair_launches(gc):
-    """timing = 1 brackets each pair launch with CUDA events; results are the
-    same as the graph-launched run."""
+    """timing = 1 brackets each pair launch with CUDA events (the four-launch
+    step, eagerly); results are the same as the graph-launched four-launch run."""
     wl = I.single_cloud(n=3000, sigma_um=0.5, z0_um=200.0, seed=12, img=32)
     outs = []
     for timing in (0, 1):
-        p = gc.gc_default_params(precision=2, img_w=32, img_h=32, graph_steps=4, timing=timing)
+        p = gc.gc_default_params(precision=2, img_w=32, img_h=32, graph_steps=4, timing=timing, fuse_small=0)
         with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
             sim.run(7)
             st = sim.stats()
@@ -554,11 +554,12 @@ def test_small_paths_equal_four_launch_step(gc, precision):
             assert_same_run(o, outs[0])
 
 
-@pytest.mark.parametrize("precision,fuse,path", [(0, 1, 2), (2, 3, 2), (2, 1, 3), (1, 1, 3)])
+@pytest.mark.parametrize("precision,fuse,path", [(0, 1, 2), (2, 3, 2), (2, 5, 3), (1, 5, 3), (2, 4, 4), (1, 4, 4),
+                                                 (2, 1, 4)])
 def test_persistent_kernel_split_runs(gc, precision, fuse, path):
-    """The persistent kernel (path 2) and the cluster kernel (path 3) stop at
-    the step limit of each gc_run and write the state back; runs split into
-    pieces give the bits of one run."""
+    """The persistent kernel (path 2), the cluster kernel (path 3) and the
+    grid-resident kernel (path 4) stop at the step limit of each gc_run and
+    write the state back; runs split into pieces give the bits of one run."""
     wl = I.single_cloud(n=700, sigma_um=0.4, z0_um=30.0, seed=19, img=32)
     outs = []
     for pieces in ([-1], [1, 7, 50, -1]):
@@ -648,15 +649,15 @@ def test_pair_shape_knobs_do_not_change_results(gc):
 
 @pytest.mark.parametrize("precision", [1, 2])
 def test_cluster_path_against_oracle_and_deterministic(gc, precision):
-    """One FP32 event of at most 1280 holes runs every step inside one
-    thread-block cluster (path 3), summing the field over the whole j range
+    """With fuse_small = 5 one FP32 event of at most 2048 holes runs every step
+    inside one thread-block cluster (path 3), summing the field over the whole j range
     and combining lanes in FP32: not the other paths' bits, but the same
     acceptance against the FP64 oracle (totals exact, sigma within 0.5 %,
     image L1 <= 1 %, per-carrier bounds of the FP32 forms), the same result
     with and without graphs, and from run to run."""
     wl = I.single_cloud(n=1000, sigma_um=0.3, z0_um=250.0, seed=71, img=64)
     ref = run_oracle(wl)
-    outs = [run_gpu(gc, wl, precision, graph_steps=gs, autotune=0) for gs in (32, 0, 32)]
+    outs = [run_gpu(gc, wl, precision, graph_steps=gs, autotune=0, fuse_small=5) for gs in (32, 0, 32)]
     for o in outs:
         assert o["stats"]["fused_path"] == 3 and o["status"] == 0
     for o in outs[1:]:
@@ -674,3 +675,75 @@ def test_cluster_path_against_oracle_and_deterministic(gc, precision):
     print(f"cluster path, precision {precision}: image L1 {l1}, same collection step {same.mean():.4f}, "
           f"|dxy| median {np.median(d[same]):.2e} um, max {d[same].max():.2e} um")
     assert same.mean() >= frac and np.median(d[same]) <= med and d[same].max() <= mx
+
+
+def acceptance(res, ref, wl, tag):
+    """The acceptance of the reduced-precision forms against the FP64 oracle:
+    totals exact, sigma_x and sigma_y within 0.5 %, image L1 <= 1 % of the
+    charge; returns (fraction collected at the oracle's step, |dxy| of those)."""
+    assert res["status"] == 0 and res["n_collected"][0] == wl.n
+    pos, rp = res["positions"], ref.positions()
+    for c in (0, 1):
+        assert pos[:, c].std() == pytest.approx(rp[:, c].std(), rel=5e-3)
+    l1 = np.abs(res["image"].astype(np.int64) - ref.image.astype(np.int64)).sum()
+    assert l1 <= 0.01 * wl.n
+    same = res["collect_step"] == ref.collect_step
+    d = np.abs(pos[:, :2] - rp[:, :2]).max(axis=1)
+    print(f"{tag}: image L1 {l1}, same collection step {same.mean():.4f}, "
+          f"|dxy| median {np.median(d[same]):.2e} um, max {d[same].max():.2e} um")
+    return same.mean(), d[same]
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_resident_path_against_oracle_and_deterministic(gc, precision):
+    """One FP32 event of at most 4096 active holes runs every step in one
+    cooperative launch of one CTA per SM (path 4): each CTA owns a fixed set
+    of holes, sums their field over the whole j range (32 lanes, FP32 lane
+    combine) and the CTAs exchange step-tagged shadow words instead of
+    passing a barrier.  Not the other paths' bits, but the same acceptance
+    against the FP64 oracle and the per-carrier bounds of the FP32 forms on
+    the 5.9 keV cloud, the same result with and without graphs and from run
+    to run; and on a 3000-hole cloud (forced with fuse_small = 4)."""
+    wl = I.xray_5p9kev()
+    ref = run_oracle(wl)
+    outs = [run_gpu(gc, wl, precision, graph_steps=gs, autotune=0) for gs in (32, 0, 32)]
+    for o in outs:
+        assert o["stats"]["fused_path"] == 4 and o["status"] == 0
+    for o in outs[1:]:
+        assert_same_run(o, outs[0])
+    frac, d = acceptance(outs[0], ref, wl, f"grid-resident path, 5.9 keV cloud, precision {precision}")
+    med, mx, fmin = XRAY_PER_CARRIER[precision]
+    assert frac >= fmin and np.median(d) <= med and d.max() <= mx
+    big = I.single_cloud(n=3000, sigma_um=0.3, z0_um=100.0, seed=72, img=64)
+    res = run_gpu(gc, big, precision, fuse_small=4)
+    assert res["stats"]["fused_path"] == 4
+    acceptance(res, run_oracle(big), big, f"grid-resident path, 3000-hole cloud, precision {precision}")
+
+
+def test_hand_over_to_resident_path_is_deterministic(gc):
+    """By default a 12,000-hole FP32 cloud starts on the four-launch step,
+    continues on the persistent kernel below 8192 active holes and on the
+    grid-resident kernel below 4096.  Every path but the last pauses at the
+    first step with at most 4096 active holes, so the step of the hand-over,
+    and so the result, does not depend on graphs or on how the run is split
+    into gc_run calls; the run meets the acceptance against the same cloud on
+    the four-launch step throughout."""
+    wl = I.single_cloud(n=12000, sigma_um=0.6, z0_um=20.0, seed=44, img=32)
+    ref = run_gpu(gc, wl, 2, fuse_small=0, autotune=0)
+    outs = []
+    for gs, pieces in ((32, [-1]), (0, [-1]), (32, [5, 40, 3, -1]), (8, [17, 200, -1])):
+        p = gc.gc_default_params(precision=2, img_w=32, img_h=32, graph_steps=gs, autotune=0)
+        with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
+            done = sum(sim.run(k)[1] for k in pieces)
+            st = sim.stats()
+            assert st["fused_path"] == 4 and st["n_active"] == 0
+            outs.append(dict(steps=done, status=0, positions=sim.positions(), image=sim.image(),
+                             collect_step=sim.collect()["collect_step"], n_offimage=sim.collect()["n_offimage"],
+                             stats=st))
+    for o in outs[1:]:
+        assert_same_run(o, outs[0])
+    a = outs[0]
+    for c in (0, 1):
+        assert a["positions"][:, c].std() == pytest.approx(ref["positions"][:, c].std(), rel=5e-3)
+    l1 = np.abs(a["image"].astype(np.int64) - ref["image"].astype(np.int64)).sum()
+    assert l1 <= 0.01 * wl.n and int(a["image"].sum()) + int(a["n_offimage"][0]) == wl.n
