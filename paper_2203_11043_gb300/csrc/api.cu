@@ -116,6 +116,14 @@ Phys make_phys(const gc_params &p) {
     ph.reflect = p.reflect_back;
     ph.stored = p.stored_charge;
     ph.stored_z = p.stored_z_um;
+    ph.f_a1 = (float)ph.a1;
+    ph.f_dt = (float)ph.dt;
+    ph.f_K = (float)ph.K;
+    ph.f_mu0 = (float)ph.mu0;
+    ph.f_inv_Ec = (float)ph.inv_Ec;
+    ph.f_beta = (float)ph.beta;
+    ph.f_inv_beta = (float)ph.inv_beta;
+    ph.f_Vth = (float)ph.Vth;
     return ph;
 }
 

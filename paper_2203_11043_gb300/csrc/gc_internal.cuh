@@ -75,6 +75,9 @@ struct Phys {
     int coulomb, diffusion, reflect;
     int stored;              // stored-charge field on (Sec. 1)
     double stored_z;         // depth of the stored-charge points, um
+    // the FP32 forms' copies (rounded to nearest on the host, as a device conversion
+    // would: a double-to-float conversion on the device is a long-latency FP64-unit step)
+    float f_a1, f_dt, f_K, f_mu0, f_inv_Ec, f_beta, f_inv_beta, f_Vth;
 };
 
 // Pair-kernel work decomposition, fixed at load time.

@@ -13,8 +13,8 @@ __device__ __forceinline__ double mobility64(const Phys &ph, double E) {
     return ph.mu0 / pow(1.0 + pow(E * ph.inv_Ec, ph.beta), ph.inv_beta);
 }
 __device__ __forceinline__ float mobility32(const Phys &ph, float E) {
-    const float t = exp2f((float)ph.beta * log2f(E * (float)ph.inv_Ec));
-    return (float)ph.mu0 * exp2f(-(float)ph.inv_beta * log2f(1.0f + t));
+    const float t = exp2f(ph.f_beta * log2f(E * ph.f_inv_Ec));
+    return ph.f_mu0 * exp2f(-ph.f_inv_beta * log2f(1.0f + t));
 }
 
 // ---- Box-Muller on the Philox bits (u_a in (0,1], u_b in [0,1)) ---------------------
@@ -37,6 +37,25 @@ __device__ __forceinline__ void normals32(uint4 b, float n[3]) {
     n[1] = r0 * sn;
     const float r1 = sqrtf(-2.0f * logf(fmaf((float)b.z, s, s)));
     n[2] = r1 * cospif(2.0f * ((float)b.w * s));
+}
+
+// ---- FP32 forms: drift (Eq. 2, v = mu E) and diffusion (Eqs. 3-4) of one step --------
+// (fx, fy, fz): the field in V/cm; n: the step's three standard normals (read only
+// with diffusion on).  The displacement in um.
+__device__ __forceinline__ void displacement32(const Phys &ph, float fx, float fy, float fz, const float n[3],
+                                               float &ddx, float &ddy, float &ddz) {
+    const float E = sqrtf(fx * fx + fy * fy + fz * fz);
+    const float mu = mobility32(ph, E);
+    const float vdt = 1e4f * mu * ph.f_dt;  // um per (V/cm)
+    ddx = vdt * fx;
+    ddy = vdt * fy;
+    ddz = vdt * fz;
+    if (ph.diffusion) {
+        const float sigma = sqrtf(2.0f * (1e8f * mu * ph.f_Vth) * ph.f_dt);
+        ddx = fmaf(sigma, n[0], ddx);
+        ddy = fmaf(sigma, n[1], ddy);
+        ddz = fmaf(sigma, n[2], ddz);
+    }
 }
 
 // ---- block-wide exclusive scan (any block of up to 1024 threads, a multiple of 32) ------------
@@ -118,6 +137,31 @@ __device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, 
             sz += dz * w;
         }
     }
+}
+
+// ---- the z check (Fig. 2) and the binning of a collected hole (Fig. 5) ----------------
+// Returns true when the hole at (x, y, z) stays active; otherwise records its
+// collection step and counts it in its event's image (or off the image).
+__device__ __forceinline__ bool collect_check(const Dev &d, int id, int e, long long step, double x, double y,
+                                              double z) {
+    const Phys &ph = d.phys;
+    if (z <= ph.z_well) {  // collected at this step
+        d.collect_step[id] = (int)step;
+        const int eu = d.ev_user[e];
+        const double fx = floor((x - d.img_origin[2 * e]) / ph.pixel);
+        const double fy = floor((y - d.img_origin[2 * e + 1]) / ph.pixel);
+        if (fx >= 0.0 && fx < (double)ph.img_w && fy >= 0.0 && fy < (double)ph.img_h) {
+            const long long pix = ((long long)eu * ph.img_h + (long long)fy) * ph.img_w + (long long)fx;
+            if (GC_GUARD(eu >= 0 && eu < d.n_events && pix >= 0 &&
+                         pix < (long long)d.n_events * ph.img_h * ph.img_w))
+                atomicAdd(&d.image[pix], 1u);
+        } else if (GC_GUARD(eu >= 0 && eu < d.n_events)) {
+            atomicAdd(&d.off_image[eu], 1ull);
+        }
+        atomicAdd(&d.ev_collected_now[e], 1);
+        return false;
+    }
+    return true;
 }
 
 // ---- per-slot step -------------------------------------------------------------------
@@ -225,19 +269,10 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                 dz += sigma * n[2];
             }
         } else {
-            const float fx = (float)ex, fy = (float)ey, fz = (float)ez;
-            const float E = sqrtf(fx * fx + fy * fy + fz * fz);
-            const float mu = mobility32(ph, E);
-            const float vdt = 1e4f * mu * (float)ph.dt;
-            float ddx = vdt * fx, ddy = vdt * fy, ddz = vdt * fz;
-            if (ph.diffusion) {
-                const float sigma = sqrtf(2.0f * (1e8f * mu * (float)ph.Vth) * (float)ph.dt);
-                float n[3];
-                normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
-                ddx = fmaf(sigma, n[0], ddx);
-                ddy = fmaf(sigma, n[1], ddy);
-                ddz = fmaf(sigma, n[2], ddz);
-            }
+            float n[3] = {0.0f, 0.0f, 0.0f};
+            if (ph.diffusion) normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
+            float ddx, ddy, ddz;
+            displacement32(ph, (float)ex, (float)ey, (float)ez, n, ddx, ddy, ddz);
             dx = ddx;
             dy = ddy;
             dz = ddz;
@@ -250,23 +285,30 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
         d.py[id] = y;
         d.pz[id] = z;
     }
-    if (z <= ph.z_well) {  // the z check: collected at this step
-        d.collect_step[id] = (int)step;
-        const int eu = d.ev_user[e];
-        const double fx = floor((x - d.img_origin[2 * e]) / ph.pixel);
-        const double fy = floor((y - d.img_origin[2 * e + 1]) / ph.pixel);
-        if (fx >= 0.0 && fx < (double)ph.img_w && fy >= 0.0 && fy < (double)ph.img_h) {
-            const long long pix = ((long long)eu * ph.img_h + (long long)fy) * ph.img_w + (long long)fx;
-            if (GC_GUARD(eu >= 0 && eu < d.n_events && pix >= 0 &&
-                         pix < (long long)d.n_events * ph.img_h * ph.img_w))
-                atomicAdd(&d.image[pix], 1u);
-        } else if (GC_GUARD(eu >= 0 && eu < d.n_events)) {
-            atomicAdd(&d.off_image[eu], 1ull);
-        }
-        atomicAdd(&d.ev_collected_now[e], 1);
-        return false;
-    }
-    return true;
+    return collect_check(d, id, e, step, x, y, z);
+}
+
+// One FP32-form step of hole `id` of event e at (x, y, z), with everything
+// that does not depend on the position update given in FP32: the unscaled
+// Eq. 6 sum (gx, gy, gz), the Eq. 1 field lin = a1 z - a2 at the hole, and
+// the step's three normals.  The field is formed in FP32 (the other paths
+// round it to FP32 as well), then the FP64 update, reflection, z check and
+// binning of advance_hole follow.  For latency-bound callers: it keeps the
+// FP64 unit off the chain but for the position update and the z check.
+__device__ __forceinline__ bool advance_hole32(const Dev &d, int id, int e, long long step, double &x, double &y,
+                                               double &z, float gx, float gy, float gz, float lin,
+                                               const float n[3]) {
+    const Phys &ph = d.phys;
+    float ddx, ddy, ddz;
+    displacement32(ph, ph.f_K * gx, ph.f_K * gy, fmaf(ph.f_K, gz, lin), n, ddx, ddy, ddz);
+    x += ddx;
+    y += ddy;
+    z += ddz;
+    if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
+    d.px[id] = x;
+    d.py[id] = y;
+    d.pz[id] = z;
+    return collect_check(d, id, e, step, x, y, z);
 }
 
 // advance_hole for the hole in slot p of the active list `cur`.

@@ -16,9 +16,19 @@
 //   * per step a CTA sums Eq. 6 for its owned holes (one warp per hole, the
 //     32 lanes over j in packed even/odd pairs, FP32 sums folded into
 //     Kahan-compensated totals every 1024 j's, lanes combined in FP32 as in
-//     the cluster kernel), integrates them in one warp (advance_hole with
-//     the field given) and publishes each hole's keep bit and next FP32
-//     shadow as three 8-byte words;
+//     the cluster kernel), integrates them in one warp and publishes each
+//     hole's keep bit and next FP32 shadow as three 8-byte words.  (Measured
+//     against two holes per warp sharing each load, and against the list
+//     split into segments for more, shorter work units: both slower at 1573
+//     holes, the second at every size, by the fixed cost of each unit's
+//     lane reduction);
+//   * the integration is a dependent chain, and on GB300 every FP64 step of
+//     it (a double operation or conversion) costs ~150-190 cycles, so it
+//     forms the field in FP32 (the sum, K and the Eq. 1 field from the FP32
+//     shadow; the other FP32 paths round the field to FP32 too) and keeps
+//     FP64 for the position update and the z check (advance_hole32); the
+//     step's normals, which do not depend on the field, come from the last
+//     warp while the others sum Eq. 6;
 //   * each word carries the step's tag beside its value and is written and
 //     read whole (8-byte relaxed accesses at GPU scope are single-copy
 //     atomic), so a reader that sees the tag has the value.  Every CTA reads
@@ -56,9 +66,11 @@ struct RsSmem {
     float sx[kRsMaxN], sy[kRsMaxN], sz[kRsMaxN];  // FP32 shadow, list order, sentinel to a multiple of 128
     float4 own_s[kRsOwn];                   // shadow of each owned hole (the i side)
     float gsum[kRsOwn][3];                  // Eq. 6 sum of each owned hole
+    float own_n[kRsOwn][3];                 // the step's normals of each owned hole (Eq. 3)
+    int own_id[kRsOwn];                     // hole id of each owned hole
     int act_own[kRsOwn];                    // owned holes still active, in owned order
-    int cnt[kRsRounds * kRsWarps];          // kept count per (round, warp), then its exclusive prefix
-    int n_own, total;
+    int cnt[kRsRounds * kRsWarps];          // kept count per (round, warp)
+    int n_own;
 };
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
@@ -82,6 +94,72 @@ __device__ __forceinline__ bool rs_tagged(unsigned long long w, unsigned tag) {
     return (unsigned)(w >> 33) == tag;
 }
 
+// Eq. 6 sum of one hole (FP32 shadow position A) over the list's `groups`
+// groups of 128 slots: lane l takes slots 4l .. 4l + 3 of each group as
+// packed even/odd pairs; FP32 sums are folded into Kahan-compensated totals
+// every kRsFoldGroups groups.  Returns on every lane the sum over the 32
+// lanes (even/odd halves first).
+template <bool KAHAN>
+__device__ __forceinline__ void rs_pair_sum(const RsSmem &S, float4 A, int groups, f2 EPS2, int lane,
+                                            float out[3]) {
+    const f2 ZERO = pack2(0.f, 0.f);
+    const f2 xi = pack2(A.x, A.x), yi = pack2(A.y, A.y), zi = pack2(A.z, A.z);
+    f2 acc[3] = {ZERO, ZERO, ZERO}, kreg[6] = {ZERO, ZERO, ZERO, ZERO, ZERO, ZERO};
+    for (int t0 = 0; t0 < groups; t0 += kRsFoldGroups) {
+        const int t1 = min(groups, t0 + kRsFoldGroups);
+#pragma unroll 1
+        for (int g = t0; g < t1; ++g) {
+            const int j = g * 128 + 4 * lane;
+            const float4 X = *reinterpret_cast<const float4 *>(S.sx + j);
+            const float4 Y = *reinterpret_cast<const float4 *>(S.sy + j);
+            const float4 Z = *reinterpret_cast<const float4 *>(S.sz + j);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const f2 xj = h ? pack2(X.z, X.w) : pack2(X.x, X.y);
+                const f2 yj = h ? pack2(Y.z, Y.w) : pack2(Y.x, Y.y);
+                const f2 zj = h ? pack2(Z.z, Z.w) : pack2(Z.x, Z.y);
+                const f2 dx = sub2(xi, xj), dy = sub2(yi, yj), dz = sub2(zi, zj);
+                f2 r2 = fma2(dx, dx, EPS2);
+                r2 = fma2(dy, dy, r2);
+                r2 = fma2(dz, dz, r2);
+                float ra, rb;
+                unpack2(r2, ra, rb);
+                const f2 inv = pack2(rsqrt_mufu(ra), rsqrt_mufu(rb));
+                const f2 inv3 = mul2(mul2(inv, inv), inv);
+                acc[0] = fma2(dx, inv3, acc[0]);
+                acc[1] = fma2(dy, inv3, acc[1]);
+                acc[2] = fma2(dz, inv3, acc[2]);
+            }
+        }
+        if (KAHAN) {  // fold this tile's sums into the compensated totals
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const f2 s0 = kreg[2 * cc], c0 = kreg[2 * cc + 1];
+                const f2 yk = sub2(acc[cc], c0), t = add2(s0, yk);
+                kreg[2 * cc + 1] = sub2(sub2(t, s0), yk);
+                kreg[2 * cc] = t;
+                acc[cc] = ZERO;
+            }
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+        float lo, hi, v;
+        if (KAHAN) {
+            float clo, chi;
+            unpack2(kreg[2 * cc], lo, hi);
+            unpack2(kreg[2 * cc + 1], clo, chi);
+            v = (lo - clo) + (hi - chi);
+        } else {
+            unpack2(acc[cc], lo, hi);
+            v = lo + hi;
+        }
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+        out[cc] = v;
+    }
+}
+
 template <bool KAHAN>
 __global__ void __launch_bounds__(kRsThreads, 1) resident_event_kernel(Dev d, unsigned long long limit_ns) {
     extern __shared__ __align__(16) unsigned char rs_smem_raw[];
@@ -97,6 +175,10 @@ __global__ void __launch_bounds__(kRsThreads, 1) resident_event_kernel(Dev d, un
     int n = c->n_active;  // at most kRsMaxN and kRsOwn * G (checked by the launcher)
     unsigned long long *const rec = d.rs_rec;
     const double ox = d.ev_origin[0], oy = d.ev_origin[1], oz = d.ev_origin[2];
+    const Phys &ph = d.phys;
+    const float c0 = (float)(ph.a1 * oz - ph.a2);  // Eq. 1 at the event origin: a1 z - a2 = c0 + a1 (z - oz)
+    const unsigned long long seed = d.ev_seed[0];
+    const int first = d.ev_first[0];
     {
         const int npad = (n + 127) & ~127;
         for (int q = tid; q < npad; q += kRsThreads) {
@@ -124,13 +206,13 @@ __global__ void __launch_bounds__(kRsThreads, 1) resident_event_kernel(Dev d, un
             y = d.py[id];
             z = d.pz[id];
             S.own_s[lane] = d.sh32[q];
+            S.own_id[lane] = id;
         }
         const unsigned m = __ballot_sync(0xffffffffu, alive);
         if (alive) S.act_own[__popc(m & lanemask_lt())] = lane;
         if (lane == 0) S.n_own = __popc(m);
     }
     __syncthreads();
-    const f2 ZERO = pack2(0.f, 0.f);
     const float eps2f = (float)d.phys.eps2;
     const f2 EPS2 = pack2(eps2f, eps2f);
     unsigned long long pairs = 0, csteps = 0;
@@ -141,74 +223,31 @@ __global__ void __launch_bounds__(kRsThreads, 1) resident_event_kernel(Dev d, un
         // ---- Eq. 6 for the owned active holes: one warp per hole, lanes over j
         const int K = S.n_own;
         const int groups = (n + 127) >> 7;
-        for (int m = warp; m < K; m += kRsWarps) {
+        if (warp == kRsWarps - 1 && ph.diffusion && lane < K) {  // the normals of this step (Philox, Box-Muller)
+            const int o = S.act_own[lane];
+            float nv[3];
+            normals32(diffusion_bits(seed, S.own_id[o] - first, step + 1), nv);
+            S.own_n[o][0] = nv[0];
+            S.own_n[o][1] = nv[1];
+            S.own_n[o][2] = nv[2];
+        }
+        for (int m = warp; m < K; m += kRsWarps) {  // one warp per owned active hole
             const int o = S.act_own[m];
-            const float4 si = S.own_s[o];
-            const f2 xi2 = pack2(si.x, si.x), yi2 = pack2(si.y, si.y), zi2 = pack2(si.z, si.z);
-            f2 ax = ZERO, ay = ZERO, az = ZERO;
-            f2 kreg[6] = {ZERO, ZERO, ZERO, ZERO, ZERO, ZERO};
-            for (int g0 = 0; g0 < groups; g0 += kRsFoldGroups) {
-                const int g1 = min(groups, g0 + kRsFoldGroups);
-#pragma unroll 2
-                for (int g = g0; g < g1; ++g) {
-                    const int j = g * 128 + 4 * lane;
-                    const float4 X = *reinterpret_cast<const float4 *>(S.sx + j);
-                    const float4 Y = *reinterpret_cast<const float4 *>(S.sy + j);
-                    const float4 Z = *reinterpret_cast<const float4 *>(S.sz + j);
+            float out[3];
+            rs_pair_sum<KAHAN>(S, S.own_s[o], groups, EPS2, lane, out);
+            if (lane == 0) {
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const f2 xj = h ? pack2(X.z, X.w) : pack2(X.x, X.y);
-                        const f2 yj = h ? pack2(Y.z, Y.w) : pack2(Y.x, Y.y);
-                        const f2 zj = h ? pack2(Z.z, Z.w) : pack2(Z.x, Z.y);
-                        const f2 dx = sub2(xi2, xj), dy = sub2(yi2, yj), dz = sub2(zi2, zj);
-                        f2 r2 = fma2(dx, dx, EPS2);
-                        r2 = fma2(dy, dy, r2);
-                        r2 = fma2(dz, dz, r2);
-                        float ra, rb;
-                        unpack2(r2, ra, rb);
-                        const f2 inv = pack2(rsqrt_mufu(ra), rsqrt_mufu(rb));
-                        const f2 inv3 = mul2(mul2(inv, inv), inv);
-                        ax = fma2(dx, inv3, ax);
-                        ay = fma2(dy, inv3, ay);
-                        az = fma2(dz, inv3, az);
-                    }
-                }
-                if (KAHAN) {  // fold this tile's sums into the compensated totals
-                    const f2 acc[3] = {ax, ay, az};
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        const f2 s0 = kreg[2 * cc], c0 = kreg[2 * cc + 1];
-                        const f2 yk = sub2(acc[cc], c0), t = add2(s0, yk);
-                        kreg[2 * cc + 1] = sub2(sub2(t, s0), yk);
-                        kreg[2 * cc] = t;
-                    }
-                    ax = ay = az = ZERO;
-                }
-            }
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {  // even/odd halves, then the 32 lanes, in FP32
-                float lo, hi, v;
-                if (KAHAN) {
-                    float clo, chi;
-                    unpack2(kreg[2 * cc], lo, hi);
-                    unpack2(kreg[2 * cc + 1], clo, chi);
-                    v = (lo - clo) + (hi - chi);
-                } else {
-                    unpack2(cc == 0 ? ax : (cc == 1 ? ay : az), lo, hi);
-                    v = lo + hi;
-                }
-#pragma unroll
-                for (int s = 16; s >= 1; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-                if (lane == 0) S.gsum[o][cc] = v;
+                for (int cc = 0; cc < 3; ++cc) S.gsum[o][cc] = out[cc];
             }
         }
         __syncthreads();
         // ---- integrate the owned holes (warp 0) and publish their words
         if (warp == 0) {
             if (alive) {
-                const bool kept = advance_hole<false, false, false, true>(
-                    d, id, 0, n, 0, step + 1, x, y, z, (double)S.gsum[lane][0], (double)S.gsum[lane][1],
-                    (double)S.gsum[lane][2]);
+                const float nv[3] = {S.own_n[lane][0], S.own_n[lane][1], S.own_n[lane][2]};
+                const bool kept = advance_hole32(d, id, 0, step + 1, x, y, z, S.gsum[lane][0], S.gsum[lane][1],
+                                                 S.gsum[lane][2],
+                                                 fmaf(ph.f_a1, S.own_s[lane].z, c0), nv);
                 const float nx = (float)(x - ox), ny = (float)(y - oy), nz = (float)(z - oz);
                 const unsigned tk = (tag << 1) | (kept ? 1u : 0u);
                 unsigned long long *w = wbuf + (b + lane * G);
@@ -292,9 +331,11 @@ __global__ void __launch_bounds__(kRsThreads, 1) resident_event_kernel(Dev d, un
             }
         }
         if (__syncthreads_or(failed)) return;  // the other CTAs' waits run out in turn
-        // ---- exclusive prefix of the kept counts in list order (round, then warp)
-        if (warp == 0) {
-            const int nv = rounds * kRsWarps;  // at most 128: four per lane
+        // ---- each warp: exclusive prefix of the kept counts in list order (round, then
+        // warp; at most 128, four per lane), then its entries of the compacted list
+        int pre[4], n_new;
+        {
+            const int nv = rounds * kRsWarps;
             int v[4], s = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -308,28 +349,27 @@ __global__ void __launch_bounds__(kRsThreads, 1) resident_event_kernel(Dev d, un
                 const int t = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += t;
             }
-            int ex = incl - s;
+            pre[0] = incl - s;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int idx = lane * 4 + i;
-                if (idx < nv) S.cnt[idx] = ex;
-                ex += v[i];
-            }
-            if (lane == 31) S.total = incl;
+            for (int i = 1; i < 4; ++i) pre[i] = pre[i - 1] + v[i - 1];
+            n_new = __shfl_sync(0xffffffffu, incl, 31);
         }
-        __syncthreads();
-        // ---- the compacted list and shadow (every read of the old list is done)
 #pragma unroll
         for (int u = 0; u < kRsRounds; ++u) {
-            if ((bal[u] >> lane) & 1u) {
-                const int q = S.cnt[u * kRsWarps + warp] + __popc(bal[u] & lanemask_lt());
-                S.ini[q] = rr[u];
-                S.sx[q] = __uint_as_float((unsigned)w[u][0]);
-                S.sy[q] = __uint_as_float((unsigned)w[u][1]);
-                S.sz[q] = __uint_as_float((unsigned)w[u][2]);
+            if (u < rounds) {  // uniform over the block
+                const int idx = u * kRsWarps + warp;  // uniform over the warp
+                const int w4 = idx & 3;
+                const int mine = w4 == 0 ? pre[0] : (w4 == 1 ? pre[1] : (w4 == 2 ? pre[2] : pre[3]));
+                const int base = __shfl_sync(0xffffffffu, mine, idx >> 2);
+                if ((bal[u] >> lane) & 1u) {
+                    const int q = base + __popc(bal[u] & lanemask_lt());
+                    S.ini[q] = rr[u];
+                    S.sx[q] = __uint_as_float((unsigned)w[u][0]);
+                    S.sy[q] = __uint_as_float((unsigned)w[u][1]);
+                    S.sz[q] = __uint_as_float((unsigned)w[u][2]);
+                }
             }
         }
-        const int n_new = S.total;
         for (int q = n_new + tid; q < ((n_new + 127) & ~127); q += kRsThreads)
             S.sx[q] = S.sy[q] = S.sz[q] = kSentinel;
         __syncthreads();
