@@ -24,6 +24,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "gc_bits.h"
+
 namespace gc {
 
 constexpr int kChunk = 4096;        // slots per integrate/compact chunk

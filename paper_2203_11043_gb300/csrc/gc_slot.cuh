@@ -142,10 +142,13 @@ __device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, 
 // ---- the z check (Fig. 2) and the binning of a collected hole (Fig. 5) ----------------
 // Returns true when the hole at (x, y, z) stays active; otherwise records its
 // collection step and counts it in its event's image (or off the image).
+// INTCMP: the test z <= z_well by integer operations (the same result, no
+// FP64 unit; the FP32 forms' updates are bound by that unit).
+template <bool INTCMP>
 __device__ __forceinline__ bool collect_check(const Dev &d, int id, int e, long long step, double x, double y,
                                               double z) {
     const Phys &ph = d.phys;
-    if (z <= ph.z_well) {  // collected at this step
+    if (INTCMP ? le_exact(z, ph.z_well) : z <= ph.z_well) {  // collected at this step
         d.collect_step[id] = (int)step;
         const int eu = d.ev_user[e];
         const double fx = floor((x - d.img_origin[2 * e]) / ph.pixel);
@@ -269,23 +272,28 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                 dz += sigma * n[2];
             }
         } else {
+            // the conversions by integer operations (gc_bits.h): the same bits, no FP64 unit;
+            // without the Coulomb and stored-charge fields the lateral field is exactly 0
             float n[3] = {0.0f, 0.0f, 0.0f};
             if (ph.diffusion) normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
             float ddx, ddy, ddz;
-            displacement32(ph, (float)ex, (float)ey, (float)ez, n, ddx, ddy, ddz);
-            dx = ddx;
-            dy = ddy;
-            dz = ddz;
+            if (ph.coulomb || ph.stored)
+                displacement32(ph, d2f_exact(ex), d2f_exact(ey), d2f_exact(ez), n, ddx, ddy, ddz);
+            else
+                displacement32(ph, 0.0f, 0.0f, d2f_exact(ez), n, ddx, ddy, ddz);
+            dx = f2d_exact(ddx);
+            dy = f2d_exact(ddy);
+            dz = f2d_exact(ddz);
         }
         x += dx;
         y += dy;
         z += dz;
-        if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
+        if (ph.reflect && (F64 ? z > ph.thickness : gt_exact(z, ph.thickness))) z = 2.0 * ph.thickness - z;
         d.px[id] = x;
         d.py[id] = y;
         d.pz[id] = z;
     }
-    return collect_check(d, id, e, step, x, y, z);
+    return collect_check<!F64>(d, id, e, step, x, y, z);
 }
 
 // One FP32-form step of hole `id` of event e at (x, y, z), with everything
@@ -301,14 +309,14 @@ __device__ __forceinline__ bool advance_hole32(const Dev &d, int id, int e, long
     const Phys &ph = d.phys;
     float ddx, ddy, ddz;
     displacement32(ph, ph.f_K * gx, ph.f_K * gy, fmaf(ph.f_K, gz, lin), n, ddx, ddy, ddz);
-    x += ddx;
-    y += ddy;
-    z += ddz;
-    if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
+    x += f2d_exact(ddx);
+    y += f2d_exact(ddy);
+    z += f2d_exact(ddz);
+    if (ph.reflect && gt_exact(z, ph.thickness)) z = 2.0 * ph.thickness - z;
     d.px[id] = x;
     d.py[id] = y;
     d.pz[id] = z;
-    return collect_check(d, id, e, step, x, y, z);
+    return collect_check<true>(d, id, e, step, x, y, z);
 }
 
 // advance_hole for the hole in slot p of the active list `cur`.

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) shadow_kernel(Dev d) {
                     d.frame_lo[q] = make_float4((float)(ox - hx), (float)(oy - hy), (float)(oz - hz), 0.f);
                 }
             }
-            d.sh32[q] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 1.0f);
+            d.sh32[q] = make_float4(d2f_exact(x - ox), d2f_exact(y - oy), d2f_exact(z - oz), 1.0f);
             if (d.ev_ext[0])
                 ext_bits = __float_as_uint(fmaxf(fabsf((float)(x - cx)),
                                                  fmaxf(fabsf((float)(y - cy)), fabsf((float)(z - cz)))));
@@ -257,8 +257,8 @@ __global__ void __launch_bounds__(kChunkThreads) compact_kernel(Dev d) {
                     if (F64) {
                         d.sh64[q] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
                     } else if (!d.tile_frames) {
-                        const float4 v = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
-                                                     (float)(d.pz[id] - oz), 1.0f);
+                        const float4 v = make_float4(d2f_exact(d.px[id] - ox), d2f_exact(d.py[id] - oy),
+                                                     d2f_exact(d.pz[id] - oz), 1.0f);
                         d.sh32[q] = v;
                         ext_bits = __float_as_uint(fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
                     }
@@ -410,8 +410,8 @@ __global__ void __launch_bounds__(kChunkThreads) small_tail_kernel(Dev d) {
         if (F64) {
             d.sh64[q] = make_double4_32a(d.px[id] - ox, d.py[id] - oy, d.pz[id] - oz, 0.0);
         } else {
-            const float4 v = make_float4((float)(d.px[id] - ox), (float)(d.py[id] - oy),
-                                         (float)(d.pz[id] - oz), 1.0f);
+            const float4 v = make_float4(d2f_exact(d.px[id] - ox), d2f_exact(d.py[id] - oy),
+                                         d2f_exact(d.pz[id] - oz), 1.0f);
             d.sh32[q] = v;
             if (ext) atomicMax(&ext[e], __float_as_uint(fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)))));
         }
