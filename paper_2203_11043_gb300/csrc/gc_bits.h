@@ -45,6 +45,28 @@ GC_HD float float_of(uint32_t u) {
     return f;
 }
 
+// The hardware conversions, for the rare inputs the integer paths leave to
+// them.  In device code they are volatile so that the compiler keeps them in
+// their branch instead of executing them for every thread.
+GC_HD double f2d_hw(float f) {
+#ifdef __CUDA_ARCH__
+    double r;
+    asm volatile("cvt.f64.f32 %0, %1;" : "=d"(r) : "f"(f));
+    return r;
+#else
+    return (double)f;
+#endif
+}
+GC_HD float d2f_hw(double d) {
+#ifdef __CUDA_ARCH__
+    float r;
+    asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(r) : "d"(d));
+    return r;
+#else
+    return (float)d;
+#endif
+}
+
 // (double)f: a normal float's exponent is rebiased (127 -> 1023) and its 23
 // mantissa bits move to the top of the 52; zeros keep their sign.
 GC_HD double f2d_exact(float f) {
@@ -53,7 +75,7 @@ GC_HD double f2d_exact(float f) {
     const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
     if (e == 0u || e == 0xffu) {
         if ((u & 0x7fffffffu) == 0u) return double_of(sign);  // +-0
-        return (double)f;                                      // subnormal, inf, NaN
+        return f2d_hw(f);                                      // subnormal, inf, NaN
     }
     return double_of(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7fffffu) << 29));
 }
@@ -65,12 +87,12 @@ GC_HD float d2f_exact(double d) {
     const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
     const int e = (int)((u >> 52) & 0x7ffu) - 896;  // the float's biased exponent
     if ((u << 1) == 0u) return float_of(sign);       // +-0
-    if (e < 1 || e > 254) return (float)d;           // subnormal, overflow, inf, NaN
+    if (e < 1 || e > 254) return d2f_hw(d);          // subnormal, overflow, inf, NaN
     const uint64_t m = u & 0xfffffffffffffull;       // 52 mantissa bits
     uint32_t r = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
     const uint32_t rest = (uint32_t)(m & 0x1fffffffu);  // the 29 dropped bits
     if (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ++r;  // may carry into the exponent
-    if ((r >> 23) >= 0xffu) return (float)d;          // rounded up to infinity
+    if ((r >> 23) >= 0xffu) return d2f_hw(d);         // rounded up to infinity
     return float_of(sign | r);
 }
 

@@ -139,6 +139,15 @@ __device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, 
     }
 }
 
+// ---- reflection at the back surface: 2 t - z (2 t is exact) -------------------------
+// Volatile, so that the compiler keeps this rare FP64 operation in its branch
+// instead of executing it for every thread.
+__device__ __forceinline__ double reflect_back(const Phys &ph, double z) {
+    double r;
+    asm volatile("sub.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(2.0 * ph.thickness), "d"(z));
+    return r;
+}
+
 // ---- the z check (Fig. 2) and the binning of a collected hole (Fig. 5) ----------------
 // Returns true when the hole at (x, y, z) stays active; otherwise records its
 // collection step and counts it in its event's image (or off the image).
@@ -178,7 +187,9 @@ __device__ __forceinline__ bool collect_check(const Dev &d, int id, int e, long 
 // on return (x, y, z) is the new position (also stored).  GIVEN: the caller
 // passes (gx, gy, gz), the sums of the per-chunk partials accumulated from 0.0
 // in chunk order (the same bits as the loop below), instead of slot p.
-template <bool F64, bool INIT, bool CG = false, bool GIVEN = false>
+// FIELD = false: neither the Coulomb nor the stored-charge field is on (the
+// O(N) path), so only Eq. 1 is formed.
+template <bool F64, bool INIT, bool CG = false, bool GIVEN = false, bool FIELD = true>
 __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_e, int p, long long step,
                                              double &x, double &y, double &z, double gx = 0.0,
                                              double gy = 0.0, double gz = 0.0) {
@@ -190,7 +201,8 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
         }
     } else {
         double ex = 0.0, ey = 0.0, ez = 0.0;
-        if (ph.coulomb && GIVEN) {
+        if (!FIELD) {
+        } else if (ph.coulomb && GIVEN) {
             ex = gx;
             ey = gy;
             ez = gz;
@@ -231,12 +243,12 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                 }
             }
         }
-        if (ph.coulomb) {
+        if (FIELD && ph.coulomb) {
             ex *= ph.K;
             ey *= ph.K;
             ez *= ph.K;
         }
-        if (ph.stored) {  // the charge already in the event's pixels (Sec. 1)
+        if (FIELD && ph.stored) {  // the charge already in the event's pixels (Sec. 1)
             if (F64) {
                 const double4_32a r = d.sh64[p];
                 double sx, sy, sz;
@@ -254,7 +266,8 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                 ez += ph.K * (double)sz;
             }
         }
-        ez += ph.a1 * z - ph.a2;  // Eq. 1
+        if (FIELD) ez += ph.a1 * z - ph.a2;  // Eq. 1
+        else ez = ph.a1 * z - ph.a2;
         double dx, dy, dz;
         if (F64) {
             const double E = sqrt(ex * ex + ey * ey + ez * ez);
@@ -277,7 +290,7 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
             float n[3] = {0.0f, 0.0f, 0.0f};
             if (ph.diffusion) normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
             float ddx, ddy, ddz;
-            if (ph.coulomb || ph.stored)
+            if (FIELD && (ph.coulomb || ph.stored))
                 displacement32(ph, d2f_exact(ex), d2f_exact(ey), d2f_exact(ez), n, ddx, ddy, ddz);
             else
                 displacement32(ph, 0.0f, 0.0f, d2f_exact(ez), n, ddx, ddy, ddz);
@@ -288,7 +301,11 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
         x += dx;
         y += dy;
         z += dz;
-        if (ph.reflect && (F64 ? z > ph.thickness : gt_exact(z, ph.thickness))) z = 2.0 * ph.thickness - z;
+        if (F64) {
+            if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
+        } else if (ph.reflect && gt_exact(z, ph.thickness)) {
+            z = reflect_back(ph, z);
+        }
         d.px[id] = x;
         d.py[id] = y;
         d.pz[id] = z;
@@ -312,7 +329,7 @@ __device__ __forceinline__ bool advance_hole32(const Dev &d, int id, int e, long
     x += f2d_exact(ddx);
     y += f2d_exact(ddy);
     z += f2d_exact(ddz);
-    if (ph.reflect && gt_exact(z, ph.thickness)) z = 2.0 * ph.thickness - z;
+    if (ph.reflect && gt_exact(z, ph.thickness)) z = reflect_back(ph, z);
     d.px[id] = x;
     d.py[id] = y;
     d.pz[id] = z;
@@ -320,12 +337,12 @@ __device__ __forceinline__ bool advance_hole32(const Dev &d, int id, int e, long
 }
 
 // advance_hole for the hole in slot p of the active list `cur`.
-template <bool F64, bool INIT, bool CG = false>
+template <bool F64, bool INIT, bool CG = false, bool FIELD = true>
 __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long long step) {
     const int id = d.act[cur][p];
     const int e = d.ev_of_id[id];
     int n_e = 0;
-    if (!INIT && d.phys.coulomb) {
+    if (!INIT && FIELD && d.phys.coulomb) {
         const int *off = d.ev_off[cur];
         n_e = off[e + 1] - off[e];
     }
@@ -339,7 +356,7 @@ __device__ __forceinline__ bool advance_slot(const Dev &d, int cur, int p, long 
         y = d.py[id];
         z = d.pz[id];
     }
-    return advance_hole<F64, INIT, CG>(d, id, e, n_e, p, step, x, y, z);
+    return advance_hole<F64, INIT, CG, false, FIELD>(d, id, e, n_e, p, step, x, y, z);
 }
 
 }  // namespace gc

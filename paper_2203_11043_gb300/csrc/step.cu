@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(kChunkThreads) occupied_pixels_kernel(Dev d) {
     }
 }
 
-template <bool F64, bool INIT>
+// FIELD = false: no Coulomb or stored-charge field (the O(N) path).
+template <bool F64, bool INIT, bool FIELD>
 __global__ void __launch_bounds__(kChunkThreads) integrate_kernel(Dev d) {
     __shared__ int s_cnt[kChunkThreads / 32];
     Ctrl *c = d.ctrl;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kChunkThreads) integrate_kernel(Dev d) {
         if (fine) {  // one slot per thread of the first kFineUnit threads
             if (threadIdx.x < kFineUnit) {
                 const int p = ch * kChunk + (u - ch * per_chunk) * kFineUnit + threadIdx.x;
-                const bool keep = p < n_act ? advance_slot<F64, INIT>(d, cur, p, step) : false;
+                const bool keep = p < n_act ? advance_slot<F64, INIT, false, FIELD>(d, cur, p, step) : false;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (lane == 0) d.keepmask[p >> 5] = m;
                 kept = __popc(m);
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kChunkThreads) integrate_kernel(Dev d) {
 #pragma unroll
             for (int k = 0; k < kChunk / kChunkThreads; ++k) {
                 const int p = ch * kChunk + k * kChunkThreads + threadIdx.x;
-                const bool keep = p < n_act ? advance_slot<F64, INIT>(d, cur, p, step) : false;
+                const bool keep = p < n_act ? advance_slot<F64, INIT, false, FIELD>(d, cur, p, step) : false;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (lane == 0) d.keepmask[p >> 5] = m;
                 kept += __popc(m);
@@ -507,12 +508,15 @@ __global__ void field_finish_kernel(Dev d, int n, double *__restrict__ E) {
 
 // ---- launchers ---------------------------------------------------------------------------------------
 cudaError_t launch_integrate(const Dev &d, bool fp64, bool init, int grid, cudaStream_t st) {
+    const bool field = d.phys.coulomb || d.phys.stored;
     if (fp64) {
-        if (init) integrate_kernel<true, true><<<grid, kChunkThreads, 0, st>>>(d);
-        else integrate_kernel<true, false><<<grid, kChunkThreads, 0, st>>>(d);
+        if (init) integrate_kernel<true, true, true><<<grid, kChunkThreads, 0, st>>>(d);
+        else if (field) integrate_kernel<true, false, true><<<grid, kChunkThreads, 0, st>>>(d);
+        else integrate_kernel<true, false, false><<<grid, kChunkThreads, 0, st>>>(d);
     } else {
-        if (init) integrate_kernel<false, true><<<grid, kChunkThreads, 0, st>>>(d);
-        else integrate_kernel<false, false><<<grid, kChunkThreads, 0, st>>>(d);
+        if (init) integrate_kernel<false, true, true><<<grid, kChunkThreads, 0, st>>>(d);
+        else if (field) integrate_kernel<false, false, true><<<grid, kChunkThreads, 0, st>>>(d);
+        else integrate_kernel<false, false, false><<<grid, kChunkThreads, 0, st>>>(d);
     }
     return cudaGetLastError();
 }
