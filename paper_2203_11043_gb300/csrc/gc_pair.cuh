@@ -245,11 +245,14 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
         }
     }
 
-    // Combine the even/odd halves and the L lanes of each i-group; write the FP64 partial.
+    // Combine the even/odd halves and the L lanes of each i-group in FP32 (a few
+    // roundings of the item's sum, within the FP32 bound of the Kahan sums: on
+    // GB300 an FP64 combination costs more FP64-unit time per item than a small
+    // event's pair work), then write the FP64 partial (an exact conversion).
     double *P = d.partial + (long long)jc * 3 * d.part_stride;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        double v[3];
+        float v[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float lo, hi;
@@ -257,21 +260,21 @@ __device__ __forceinline__ void pair_item_fp32_j(const Dev &d, int e_start, int 
                 float clo, chi;
                 unpack2(kreg[r * 6 + 2 * c], lo, hi);
                 unpack2(kreg[r * 6 + 2 * c + 1], clo, chi);
-                v[c] = ((double)lo - (double)clo) + ((double)hi - (double)chi);
-                if (H16) v[c] *= (double)scale * (double)scale;
+                v[c] = (lo - clo) + (hi - chi);
             } else {
                 unpack2(c == 0 ? ax[r] : (c == 1 ? ay[r] : az[r]), lo, hi);
-                v[c] = (double)lo + (double)hi;
+                v[c] = lo + hi;
             }
+            if (H16) v[c] *= scale * scale;  // a power of two: exact
 #pragma unroll
             for (int o = 1; o < L; o <<= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
         }
         const int il = il0 + r * STRIDE;
         if (ph == 0 && il < n_e && GC_GUARD(e_start + il < d.n_total)) {
             const long long p = e_start + il;
-            P[p] = v[0];
-            P[d.part_stride + p] = v[1];
-            P[2 * d.part_stride + p] = v[2];
+            P[p] = f2d_exact(v[0]);
+            P[d.part_stride + p] = f2d_exact(v[1]);
+            P[2 * d.part_stride + p] = f2d_exact(v[2]);
         }
     }
 }
