@@ -277,7 +277,10 @@ gc_status gc_coulomb_field_noalloc(const double *xyz_dev, int64_t n, double soft
  * otherwise): what = 1 makes the next gc_load_carriers of `s` upload event
  * offsets that do not match its carriers.  The load then succeeds, no kernel
  * uses the offsets (the step-0 pass checks them first), and gc_run returns
- * GC_ERR_DEVICE_CHECK.  what = 0 cancels. */
+ * GC_ERR_DEVICE_CHECK.  what = 2 makes one CTA of the next grid-resident
+ * launch of `s` withhold its first step's words: every other CTA's bounded
+ * wait runs out (1 s) and gc_run returns GC_ERR_DEVICE_TIMEOUT, with nothing
+ * faulted or hung.  what = 0 cancels. */
 gc_status gc_debug_inject(gc_sim *s, int32_t what);
 
 /* Self-test of the library's bounded device-side wait (the grid barrier of

@@ -887,8 +887,10 @@ gc_status gc_load_carriers(gc_sim *s, const double *xyz, int64_t n, const int64_
     }
     ioff[E] = pos;
 #ifdef GC_DEBUG
-    if (s->inject == 1) ioff[E] = pos + 7;  // planted: the offsets no longer match the carriers
-    s->inject = 0;
+    if (s->inject == 1) {
+        ioff[E] = pos + 7;  // planted: the offsets no longer match the carriers
+        s->inject = 0;
+    }
 #endif
     // tile frames (FP32 forms, on request, when some event has >= small_n
     // holes): the large events in spatial (Morton) order
@@ -1129,8 +1131,12 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
                 // one event: the whole remaining loop on every SM, each CTA owning
                 // a fixed set of holes, no grid barrier between steps
                 s->fused_ran = 4;
-                GC_CUDA(launch_resident_event(s->dev, s->p.precision, na0, s->sm_count, kDeviceWaitLimitS,
-                                              s->stream));
+                Dev dd = s->dev;
+#ifdef GC_DEBUG
+                dd.dbg_withhold = s->inject == 2;  // planted: one CTA withholds its first words
+                if (s->inject == 2) s->inject = 0;
+#endif
+                GC_CUDA(launch_resident_event(dd, s->p.precision, na0, s->sm_count, kDeviceWaitLimitS, s->stream));
                 r = read_ctrl(s);
                 if (r != GC_OK) return r;
                 if (s->h_ctrl->error) {
@@ -1503,7 +1509,7 @@ gc_status gc_coulomb_field(const double *xyz_dev, int64_t n, double softening_um
 }
 
 gc_status gc_debug_inject(gc_sim *s, int32_t what) {
-    if (!s || what < 0 || what > 1) return GC_ERR_PARAM;
+    if (!s || what < 0 || what > 2) return GC_ERR_PARAM;
 #ifdef GC_DEBUG
     s->inject = what;
     return GC_OK;

@@ -137,6 +137,8 @@ struct Dev {
     // grid-resident single-event kernel: each hole's published words (FP32
     // shadow coordinate + step tag + keep bit), [parity][coordinate][slot at launch]
     unsigned long long *rs_rec;
+    int dbg_withhold;        // GC_DEBUG builds: CTA 1 of the grid-resident kernel withholds its
+                             // first step's words (gc_debug_inject 2)
     Ctrl *ctrl;
     int n_total;
     int n_events;

@@ -251,9 +251,16 @@ __global__ void __launch_bounds__(kRsThreads, 1) resident_event_kernel(Dev d, un
                 const float nx = d2f_exact(x - ox), ny = d2f_exact(y - oy), nz = d2f_exact(z - oz);
                 const unsigned tk = (tag << 1) | (kept ? 1u : 0u);
                 unsigned long long *w = wbuf + (b + lane * G);
-                st_relaxed_u64(w, rs_word(nx, tk));
-                st_relaxed_u64(w + kRsMaxN, rs_word(ny, tk));
-                st_relaxed_u64(w + 2 * kRsMaxN, rs_word(nz, tk));
+#ifdef GC_DEBUG
+                const bool withhold = d.dbg_withhold && b == 1 && k == 0;  // planted: the others' waits run out
+#else
+                constexpr bool withhold = false;
+#endif
+                if (!withhold) {
+                    st_relaxed_u64(w, rs_word(nx, tk));
+                    st_relaxed_u64(w + kRsMaxN, rs_word(ny, tk));
+                    st_relaxed_u64(w + 2 * kRsMaxN, rs_word(nz, tk));
+                }
                 if (kept) S.own_s[lane] = make_float4(nx, ny, nz, 0.0f);
                 alive = kept;
             }

@@ -8,6 +8,10 @@
     on the host before upload (gc_debug_inject) -- is caught on the device
     before any kernel uses the offsets: gc_run returns GC_ERR_DEVICE_CHECK,
     nothing faults, and the device stays usable.
+  * A planted missing peer -- one CTA of the grid-resident kernel withholds
+    its first step's words -- makes every other CTA's bounded wait run out:
+    gc_run returns GC_ERR_DEVICE_TIMEOUT within seconds, nothing faults or
+    hangs, and the device stays usable.
 
 The debug library runs in a child process (GCORECCD_DEBUG=1), since this
 process has the release library loaded.
@@ -55,6 +59,22 @@ try:
         out["inject"] = int(e.status)
 finally:
     gc.gc_destroy(h)
+# planted: one CTA of the grid-resident kernel withholds its first words
+import time
+wx = I.xray_5p9kev()
+h = gc.gc_create(gc.gc_default_params(img_w=wx.img_w, img_h=wx.img_h, fuse_small=4))
+try:
+    gc.gc_load_carriers(h, wx.xyz, wx.ev_off, wx.seeds, wx.img_origin)
+    gc.gc_debug_inject(h, 2)
+    t0 = time.time()
+    try:
+        gc.gc_run(h, -1)
+        out["withhold"] = "no error"
+    except gc.GcError as e:
+        out["withhold"] = int(e.status)
+    out["withhold_s"] = time.time() - t0
+finally:
+    gc.gc_destroy(h)
 # the device is usable afterwards
 p = gc.gc_default_params(img_w=16, img_h=16)
 with gc.Simulation(p, wl.xyz, wl.ev_off, wl.seeds, wl.img_origin) as sim:
@@ -99,6 +119,7 @@ def test_debug_build_checks_are_silent_then_catch_a_planted_fault(gc, tmp_path):
     assert r.returncode == 0, r.stderr[-3000:]
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["inject"] == gc.GC_ERR_DEVICE_CHECK
+    assert out["withhold"] == gc.GC_ERR_DEVICE_TIMEOUT and out["withhold_s"] < 30, out
     assert out["after"] == gc.GC_OK
     for name, wl, kw in cases():
         assert out[name]["status"] == gc.GC_OK, name
