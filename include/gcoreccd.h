@@ -82,7 +82,9 @@ typedef struct {
     int32_t autotune;      /* 1: pick the pair-kernel shape (carriers per thread, kernel variant,
                               resident blocks per SM, j-chunk length, 4-lane threshold) by timing
                               candidates on sampled work items of the loaded carriers; the choice
-                              is cached in the process per device, form and event-size histogram */
+                              is cached in the process per device, form and event-size histogram.
+                              Skipped for one FP32 event that the grid-resident kernel runs
+                              entirely (at most 4096 holes, fuse_small 1 or 4) */
     int32_t newton;        /* 1: one Newton step after the MUFU rsqrt (FP32 forms) */
     int32_t jchunk;        /* j-chunk length of a pair work item; 0 = automatic */
     int32_t pair_R;        /* carriers per thread in the FP32 pair kernel (2, 4, 8); 0 = automatic */

@@ -605,7 +605,10 @@ gc_status choose_shape(gc_sim *s, const std::vector<long long> &sizes) {
     for (long long n : sizes) n_max = std::max(n_max, n);
     TuneKnobs def;
     if (s->p.pair_R) def.R = s->p.pair_R;
-    const bool tune = s->p.autotune && s->phys.coulomb && s->n > 0;
+    // one FP32 event small enough for the grid-resident kernel runs every step
+    // there, and that kernel does not use the pair kernel's shape: no search
+    const bool resident_only = s->resident_ok && s->n <= kResidentPathMax;
+    const bool tune = s->p.autotune && s->phys.coulomb && s->n > 0 && !resident_only;
     auto fits = [&](const PairShape &sh) {
         return sh.n_blocks > 0 && (n_max + sh.jchunk - 1) / sh.jchunk <= s->part_cap_chunks;
     };

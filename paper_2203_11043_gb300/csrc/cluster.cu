@@ -171,9 +171,9 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_event_kernel(Dev d) {
             kept = advance_hole<false, false, true, true>(d, id, 0, n, p, step + 1, x, y, z, gsum[0], gsum[1],
                                                          gsum[2])
                        ? 1 : 0;
-            nsx = d2f_exact(x - ox);
-            nsy = d2f_exact(y - oy);
-            nsz = d2f_exact(z - oz);
+            nsx = (float)(x - ox);
+            nsy = (float)(y - oy);
+            nsz = (float)(z - oz);
         }
         // every CTA's staging area gets the keep byte and next shadow of this CTA's slots
         const int src = lane & ~3;

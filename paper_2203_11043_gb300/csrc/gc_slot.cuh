@@ -139,6 +139,18 @@ __device__ __forceinline__ void stored_field(const Dev &d, int e, T rx0, T ry0, 
     }
 }
 
+// ---- conversions: by integer operations (INT) or by the hardware -------------------
+template <bool INT>
+__device__ __forceinline__ float cvt_d2f(double v) {
+    if constexpr (INT) return d2f_exact(v);
+    else return (float)v;
+}
+template <bool INT>
+__device__ __forceinline__ double cvt_f2d(float v) {
+    if constexpr (INT) return f2d_exact(v);
+    else return (double)v;
+}
+
 // ---- reflection at the back surface: 2 t - z (2 t is exact) -------------------------
 // Volatile, so that the compiler keeps this rare FP64 operation in its branch
 // instead of executing it for every thread.
@@ -194,6 +206,11 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                                              double &x, double &y, double &z, double gx = 0.0,
                                              double gy = 0.0, double gz = 0.0) {
     const Phys &ph = d.phys;
+    // INT: the FP32 forms' conversions and threshold tests by integer operations
+    // (gc_bits.h; the same bits) where the FP64 unit's throughput bounds the
+    // kernel -- the integrate kernel, one thread per hole.  The latency-bound
+    // fused kernels (CG) keep the hardware operations, whose latency is lower.
+    constexpr bool INT = !F64 && !CG;
     if (INIT) {
         if (ph.reflect && z > ph.thickness) {
             z = 2.0 * ph.thickness - z;
@@ -285,23 +302,22 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                 dz += sigma * n[2];
             }
         } else {
-            // the conversions by integer operations (gc_bits.h): the same bits, no FP64 unit;
             // without the Coulomb and stored-charge fields the lateral field is exactly 0
             float n[3] = {0.0f, 0.0f, 0.0f};
             if (ph.diffusion) normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
             float ddx, ddy, ddz;
             if (FIELD && (ph.coulomb || ph.stored))
-                displacement32(ph, d2f_exact(ex), d2f_exact(ey), d2f_exact(ez), n, ddx, ddy, ddz);
+                displacement32(ph, cvt_d2f<INT>(ex), cvt_d2f<INT>(ey), cvt_d2f<INT>(ez), n, ddx, ddy, ddz);
             else
-                displacement32(ph, 0.0f, 0.0f, d2f_exact(ez), n, ddx, ddy, ddz);
-            dx = f2d_exact(ddx);
-            dy = f2d_exact(ddy);
-            dz = f2d_exact(ddz);
+                displacement32(ph, 0.0f, 0.0f, cvt_d2f<INT>(ez), n, ddx, ddy, ddz);
+            dx = cvt_f2d<INT>(ddx);
+            dy = cvt_f2d<INT>(ddy);
+            dz = cvt_f2d<INT>(ddz);
         }
         x += dx;
         y += dy;
         z += dz;
-        if (F64) {
+        if (!INT) {
             if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
         } else if (ph.reflect && gt_exact(z, ph.thickness)) {
             z = reflect_back(ph, z);
@@ -310,7 +326,7 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
         d.py[id] = y;
         d.pz[id] = z;
     }
-    return collect_check<!F64>(d, id, e, step, x, y, z);
+    return collect_check<INT>(d, id, e, step, x, y, z);
 }
 
 // One FP32-form step of hole `id` of event e at (x, y, z), with everything
@@ -326,14 +342,14 @@ __device__ __forceinline__ bool advance_hole32(const Dev &d, int id, int e, long
     const Phys &ph = d.phys;
     float ddx, ddy, ddz;
     displacement32(ph, ph.f_K * gx, ph.f_K * gy, fmaf(ph.f_K, gz, lin), n, ddx, ddy, ddz);
-    x += f2d_exact(ddx);
-    y += f2d_exact(ddy);
-    z += f2d_exact(ddz);
-    if (ph.reflect && gt_exact(z, ph.thickness)) z = reflect_back(ph, z);
+    x += ddx;  // hardware conversions and tests: on this latency chain they are faster
+    y += ddy;  // than the integer forms (measured in the grid-resident kernel)
+    z += ddz;
+    if (ph.reflect && z > ph.thickness) z = 2.0 * ph.thickness - z;
     d.px[id] = x;
     d.py[id] = y;
     d.pz[id] = z;
-    return collect_check<true>(d, id, e, step, x, y, z);
+    return collect_check<false>(d, id, e, step, x, y, z);
 }
 
 // advance_hole for the hole in slot p of the active list `cur`.

@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kRsThreads, 1) resident_event_kernel(Dev d, un
                 const bool kept = advance_hole32(d, id, 0, step + 1, x, y, z, S.gsum[lane][0], S.gsum[lane][1],
                                                  S.gsum[lane][2],
                                                  fmaf(ph.f_a1, S.own_s[lane].z, c0), nv);
-                const float nx = d2f_exact(x - ox), ny = d2f_exact(y - oy), nz = d2f_exact(z - oz);
+                const float nx = (float)(x - ox), ny = (float)(y - oy), nz = (float)(z - oz);
                 const unsigned tk = (tag << 1) | (kept ? 1u : 0u);
                 unsigned long long *w = wbuf + (b + lane * G);
 #ifdef GC_DEBUG

@@ -69,7 +69,7 @@ __device__ __forceinline__ void se_tile_done(const Dev &d, int n, int local, int
             if constexpr (F64)
                 wr[id] = make_double4_32a(x - ox, y - oy, z - oz, 0.0);
             else
-                wr[id] = make_float4(d2f_exact(x - ox), d2f_exact(y - oy), d2f_exact(z - oz), 1.0f);
+                wr[id] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 1.0f);
         }
         keep[q] = kept ? 1 : 0;
     }

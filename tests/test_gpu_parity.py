@@ -714,6 +714,10 @@ def test_resident_path_against_oracle_and_deterministic(gc, precision):
     frac, d = acceptance(outs[0], ref, wl, f"grid-resident path, 5.9 keV cloud, precision {precision}")
     med, mx, fmin = XRAY_PER_CARRIER[precision]
     assert frac >= fmin and np.median(d) <= med and d.max() <= mx
+    # with the autotuner on (the default) the load searches no pair-kernel shape: this
+    # path does not use it
+    st = run_gpu(gc, wl, precision)["stats"]
+    assert st["fused_path"] == 4 and st["tune_candidates"] == 0 and st["tune_cached"] == 0
     big = I.single_cloud(n=3000, sigma_um=0.3, z0_um=100.0, seed=72, img=64)
     res = run_gpu(gc, big, precision, fuse_small=4)
     assert res["stats"]["fused_path"] == 4
