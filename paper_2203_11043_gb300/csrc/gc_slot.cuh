@@ -252,7 +252,11 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                 }
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
-                    if (jc0 + u < js) {
+                    if (jc0 + u == 0) {  // the first chunk (no addition to zero)
+                        ex = v[u][0];
+                        ey = v[u][1];
+                        ez = v[u][2];
+                    } else if (jc0 + u < js) {
                         ex += v[u][0];
                         ey += v[u][1];
                         ez += v[u][2];
@@ -260,32 +264,34 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                 }
             }
         }
-        if (FIELD && ph.coulomb) {
-            ex *= ph.K;
-            ey *= ph.K;
-            ez *= ph.K;
-        }
-        if (FIELD && ph.stored) {  // the charge already in the event's pixels (Sec. 1)
-            if (F64) {
-                const double4_32a r = d.sh64[p];
-                double sx, sy, sz;
-                stored_field<double>(d, e, r.x, r.y, r.z, sx, sy, sz);
-                ex += ph.K * sx;
-                ey += ph.K * sy;
-                ez += ph.K * sz;
-            } else {  // the FP32 shadow may be tile-relative: use the event frame here
-                const float rx = (float)(x - d.ev_origin[3 * e]), ry = (float)(y - d.ev_origin[3 * e + 1]),
-                            rz = (float)(z - d.ev_origin[3 * e + 2]);
-                float sx, sy, sz;
-                stored_field<float>(d, e, rx, ry, rz, sx, sy, sz);
-                ex += ph.K * (double)sx;
-                ey += ph.K * (double)sy;
-                ez += ph.K * (double)sz;
-            }
-        }
-        if (FIELD) ez += ph.a1 * z - ph.a2;  // Eq. 1
-        else ez = ph.a1 * z - ph.a2;
         double dx, dy, dz;
+        if (F64 || (FIELD && ph.stored)) {  // the field in FP64 (the FP64 form; stored charge)
+            if (FIELD && ph.coulomb) {
+                ex *= ph.K;
+                ey *= ph.K;
+                ez *= ph.K;
+            }
+            if (FIELD && ph.stored) {  // the charge already in the event's pixels (Sec. 1)
+                if (F64) {
+                    const double4_32a r = d.sh64[p];
+                    double sx, sy, sz;
+                    stored_field<double>(d, e, r.x, r.y, r.z, sx, sy, sz);
+                    ex += ph.K * sx;
+                    ey += ph.K * sy;
+                    ez += ph.K * sz;
+                } else {  // the FP32 shadow may be tile-relative: use the event frame here
+                    const float rx = (float)(x - d.ev_origin[3 * e]), ry = (float)(y - d.ev_origin[3 * e + 1]),
+                                rz = (float)(z - d.ev_origin[3 * e + 2]);
+                    float sx, sy, sz;
+                    stored_field<float>(d, e, rx, ry, rz, sx, sy, sz);
+                    ex += ph.K * (double)sx;
+                    ey += ph.K * (double)sy;
+                    ez += ph.K * (double)sz;
+                }
+            }
+            if (FIELD) ez += ph.a1 * z - ph.a2;  // Eq. 1
+            else ez = ph.a1 * z - ph.a2;
+        }
         if (F64) {
             const double E = sqrt(ex * ex + ey * ey + ez * ez);
             const double mu = mobility64(ph, E);
@@ -302,14 +308,26 @@ __device__ __forceinline__ bool advance_hole(const Dev &d, int id, int e, int n_
                 dz += sigma * n[2];
             }
         } else {
-            // without the Coulomb and stored-charge fields the lateral field is exactly 0
             float n[3] = {0.0f, 0.0f, 0.0f};
             if (ph.diffusion) normals32(diffusion_bits(d.ev_seed[e], id - d.ev_first[e], step), n);
+            // the FP32 forms round the field to FP32: formed in FP32 from the FP64
+            // sums (K times each sum, plus Eq. 1), as the grid-resident kernel does;
+            // without the Coulomb and stored-charge fields the lateral field is 0
+            float fx = 0.0f, fy = 0.0f, fz;
+            if (FIELD && ph.stored) {
+                fx = cvt_d2f<INT>(ex);
+                fy = cvt_d2f<INT>(ey);
+                fz = cvt_d2f<INT>(ez);
+            } else {
+                fz = cvt_d2f<INT>(ph.a1 * z - ph.a2);  // Eq. 1
+                if (FIELD && ph.coulomb) {
+                    fx = ph.f_K * cvt_d2f<INT>(ex);
+                    fy = ph.f_K * cvt_d2f<INT>(ey);
+                    fz = fmaf(ph.f_K, cvt_d2f<INT>(ez), fz);
+                }
+            }
             float ddx, ddy, ddz;
-            if (FIELD && (ph.coulomb || ph.stored))
-                displacement32(ph, cvt_d2f<INT>(ex), cvt_d2f<INT>(ey), cvt_d2f<INT>(ez), n, ddx, ddy, ddz);
-            else
-                displacement32(ph, 0.0f, 0.0f, cvt_d2f<INT>(ez), n, ddx, ddy, ddz);
+            displacement32(ph, fx, fy, fz, n, ddx, ddy, ddz);
             dx = cvt_f2d<INT>(ddx);
             dy = cvt_f2d<INT>(ddy);
             dz = cvt_f2d<INT>(ddz);
