@@ -121,7 +121,10 @@ typedef struct {
                               carrier's field in one piece with the lanes combined in FP32 (the
                               same FP32 error bound, not the same bits).  Not used with newton,
                               tile frames, stored charge or timing */
-    int32_t reserved0;
+    int32_t resident_ctas; /* CTAs of the grid-resident kernel (fuse_small 1 or 4); 0 (default) =
+                              one per 8 active holes at the launch, at most one per SM.  Clamped
+                              to [ceil(n / 32), SMs] (each CTA owns at most 32 holes).  The
+                              results do not depend on it, only the time */
 } gc_params;
 
 typedef struct gc_sim gc_sim;

@@ -88,6 +88,7 @@ gc_status validate(const gc_params *p) {
          p->stored_charge | p->tile_frames) & ~1)
         return GC_ERR_PARAM;
     if (p->fuse_small < 0 || p->fuse_small > 5) return GC_ERR_PARAM;
+    if (p->resident_ctas < 0) return GC_ERR_PARAM;
     if (p->pair_R != 0 && p->pair_R != 2 && p->pair_R != 4 && p->pair_R != 8) return GC_ERR_PARAM;
     return GC_OK;
 }
@@ -1139,7 +1140,8 @@ gc_status gc_run(gc_sim *s, int64_t steps, int64_t *steps_done) {
                 dd.dbg_withhold = s->inject == 2;  // planted: one CTA withholds its first words
                 if (s->inject == 2) s->inject = 0;
 #endif
-                GC_CUDA(launch_resident_event(dd, s->p.precision, na0, s->sm_count, kDeviceWaitLimitS, s->stream));
+                GC_CUDA(launch_resident_event(dd, s->p.precision, na0, s->sm_count, s->p.resident_ctas,
+                                              kDeviceWaitLimitS, s->stream));
                 r = read_ctrl(s);
                 if (r != GC_OK) return r;
                 if (s->h_ctrl->error) {

@@ -75,14 +75,14 @@ bool cluster_path_available(int precision, int n);
 cudaError_t launch_cluster_event(const Dev &d, int precision, int n, cudaStream_t st);
 // Grid-resident single-event kernel (one event of at most 4096 active holes,
 // FP32 or FP32 + Kahan): every step until completion or the step limit in one
-// cooperative launch of resident_grid(sm_count, n) CTAs, each owning a fixed
+// cooperative launch of resident_grid(sm_count, n, ctas) CTAs, each owning a fixed
 // set of holes, exchanging step-tagged words instead of a grid barrier; its
 // waits give up after limit_s (kErrBarrierTimeout).  The words take
 // resident_words_bytes() of device memory (Dev::rs_rec).
 size_t resident_words_bytes();
-int resident_grid(int sm_count, int n);
+int resident_grid(int sm_count, int n, int ctas);
 bool resident_path_available(int precision, int n, int sm_count);
-cudaError_t launch_resident_event(const Dev &d, int precision, int n, int sm_count, double limit_s,
+cudaError_t launch_resident_event(const Dev &d, int precision, int n, int sm_count, int ctas, double limit_s,
                                   cudaStream_t st);
 // Runs a barrier that can never complete on `grid` co-resident blocks; the
 // error bits it leaves (kErrBarrierTimeout expected) go to *error_bits.

@@ -59,7 +59,7 @@ class GcParams(ctypes.Structure):
         ("tile_frames", ctypes.c_int32),
         ("stored_z_um", ctypes.c_double),
         ("fuse_small", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("resident_ctas", ctypes.c_int32),
     ]
 
 

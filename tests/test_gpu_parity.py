@@ -751,3 +751,17 @@ def test_hand_over_to_resident_path_is_deterministic(gc):
         assert a["positions"][:, c].std() == pytest.approx(ref["positions"][:, c].std(), rel=5e-3)
     l1 = np.abs(a["image"].astype(np.int64) - ref["image"].astype(np.int64)).sum()
     assert l1 <= 0.01 * wl.n and int(a["image"].sum()) + int(a["n_offimage"][0]) == wl.n
+
+
+def test_resident_results_do_not_depend_on_the_grid(gc):
+    """Each hole's Eq. 6 sum in the grid-resident kernel runs over the whole
+    list in list order with the same lane split, whichever CTA owns the hole,
+    so the number of CTAs (resident_ctas; 0 = automatic) changes the time,
+    not the bits: the 5.9 keV cloud on 16, 50 and 152 CTAs and on the
+    automatic grid."""
+    wl = I.xray_5p9kev()
+    outs = [run_gpu(gc, wl, 2, fuse_small=4, resident_ctas=g) for g in (0, 50, 152, 16)]
+    for o in outs:
+        assert o["stats"]["fused_path"] == 4 and o["status"] == 0
+    for o in outs[1:]:
+        assert_same_run(o, outs[0])
