@@ -22,6 +22,9 @@ int main(void) {
     bad.fuse_small = 6;
     EXPECT(gc_create(&bad, NULL, &s) == GC_ERR_PARAM);
     bad = p;
+    bad.resident_ctas = -1;
+    EXPECT(gc_create(&bad, NULL, &s) == GC_ERR_PARAM);
+    bad = p;
     bad.img_w = 0;
     EXPECT(gc_create(&bad, NULL, &s) == GC_ERR_PARAM);
     bad = p;
