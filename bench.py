@@ -428,7 +428,7 @@ def main():
                     help="with --to-completion: 1 adds the field of the charge stored in the pixels")
     ap.add_argument("--per-event", type=int, default=0,
                     help="with --to-completion: also run the first M events one simulation each")
-    ap.add_argument("--fuse-small", type=int, default=1, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--fuse-small", type=int, default=1, choices=[0, 1, 2, 3, 4, 5],
                     help="small-workload path (gc_params.fuse_small; 1 = automatic)")
     ap.add_argument("--precision", default="fp32k", choices=sorted(PRECISIONS),
                     help="with --to-completion: arithmetic of the pair sum")
