@@ -50,8 +50,8 @@ namespace {
 // One FP32 / FP32 + Kahan event of at most this many active holes takes the
 // grid-resident kernel by default.  Measured per step to completion (clouds at
 // 300 um, FP32 + Kahan): 256 holes 3.2 us there, 4.7 us in the cluster kernel,
-// 9.7 us in the persistent kernel; 1573 holes 5.5 us against 15.8 and 14.7 us;
-// 4096 holes 12.8 us against 28.9 us in the persistent kernel.
+// 7.9 us in the persistent kernel; 1573 holes 5.5 us against 15.6 and 11.9 us;
+// 4096 holes 12.8 us against 26.5 us in the persistent kernel.
 constexpr int kResidentPathMax = 4096;
 
 // Longest a device-side wait (a grid barrier of the persistent kernel, a
